@@ -1,0 +1,150 @@
+/*
+ * purl.h -- C ABI of libpurl: the PowerURV rank-revealing factorization
+ * (Gopal & Martinsson, arXiv:1812.06007) on one NVIDIA GB300 (sm_103a).
+ *
+ * Given A (m x n, m >= n) the library computes A = U R V^T with
+ *   U  m x n, orthonormal columns;  R  n x n upper triangular, diag(R) >= 0;
+ *   V  n x n orthogonal,
+ * by the PowerURV algorithm of Section 3 of the paper:
+ *   1. draw G (n x n) with i.i.d. N(0,1) entries from `seed`;
+ *   2. q power steps Y <- A^T (A Y), starting from Y = G, re-orthonormalising
+ *      after every product with A or A^T when `reorth` != 0 (Section 3, third
+ *      paragraph); Eq. (5): (A^T A)^q G = V Z by an unpivoted Householder QR;
+ *   3. Eq. (6): A V = U R by a second unpivoted Householder QR.
+ * With q = 0 this is the DDH-URV algorithm (Section 2.2).
+ *
+ * Conventions shared by every entry point:
+ *   - All matrices are column-major FP64 in DEVICE memory with a leading
+ *     dimension ld >= rows (ld >= 1 when rows == 0).  The caller owns every
+ *     buffer; the library never frees or keeps a caller pointer past the call.
+ *   - Outputs must not alias inputs or each other.
+ *   - Work is enqueued on `stream` (0 = legacy default stream) and the call
+ *     returns without synchronising.  The return value reports argument and
+ *     launch errors only.  Errors that can only be seen on the device (a
+ *     bounded wait that ran out) are recorded in a per-device status word read
+ *     with purl_device_status().
+ *   - Argument errors return -i for the i-th argument (LAPACK style, counting
+ *     from 1), PURL_ERR_SHAPE when m < n (factor A^T instead: Section 1 notes
+ *     that a URV of A^T gives a ULV of A and vice versa).
+ *   - Every routine is deterministic: the same inputs on the same GPU give the
+ *     same bits.
+ */
+#ifndef PURL_H_
+#define PURL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PURL_OK 0
+#define PURL_ERR_SHAPE (-100)  /* m < n */
+#define PURL_ERR_NONFINITE 1   /* reserved: non-finite input detected */
+#define PURL_ERR_TIMEOUT 2     /* a bounded device-side wait ran out */
+#define PURL_ERR_CUDA 3        /* a CUDA runtime call failed */
+#define PURL_ERR_NOMEM 4       /* workspace allocation failed or too small */
+#define PURL_ERR_UNSUPPORTED 5 /* this GPU / build cannot run the request */
+
+/* precision modes for purl_urv_factor_ex / purl_qr */
+#define PURL_MODE_FP64 0
+/* Power-step products A Y and A^T Z on BF16 tensor cores (FP32 accumulate);
+ * A V, every QR trailing update and Q formation as split-BF16 compensated
+ * products; Householder panels in FP64. */
+#define PURL_MODE_MIXED_BF16 2
+
+/* Human-readable text for a status code (static storage). */
+const char *purl_status_str(int status);
+
+/* Library version string, e.g. "purl 0.1.0 sm_103a". */
+const char *purl_version(void);
+
+/*
+ * purl_urv_factor -- PowerURV in FP64 (Section 3, Eqs. (5)-(6)).
+ *   m, n     A is m x n, m >= n >= 0.
+ *   A, lda   input, not modified.
+ *   q        number of power steps, q >= 0 (q = 0: DDH-URV, Section 2.2).
+ *   reorth   nonzero: orthonormalise (Householder QR, explicit Q with a
+ *            nonnegative R diagonal) after every product with A or A^T;
+ *            the last one is the QR of Eq. (5) itself.
+ *   seed     key of the Gaussian draw (see purl_gaussian, stream 0).
+ *   U, ldu   output m x n.   R, ldr  output n x n (zeros below the
+ *   diagonal, diag >= 0).    V, ldv  output n x n.
+ * Workspace is allocated stream-ordered (cudaMallocAsync) and released on
+ * `stream` before the call returns; use purl_urv_factor_ex to pass your own.
+ */
+int purl_urv_factor(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                    double *U, int ldu, double *R, int ldr, double *V, int ldv,
+                    cudaStream_t stream);
+
+/*
+ * purl_urv_factor_ex -- as purl_urv_factor with a precision `mode` and an
+ * optional caller workspace (device memory, 256-byte aligned, at least
+ * purl_urv_workspace_bytes(m, n, mode) bytes; NULL = allocate on `stream`).
+ */
+int purl_urv_factor_ex(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                       double *U, int ldu, double *R, int ldr, double *V, int ldv, int mode,
+                       void *workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* Workspace bytes purl_urv_factor_ex needs for (m, n, mode); 0 on bad args. */
+size_t purl_urv_workspace_bytes(int m, int n, int mode);
+
+/*
+ * purl_gaussian -- the Gaussian matrix G of Section 3 (the paper fixes no
+ * generator; this library's is defined here).  Element e of the rows x cols
+ * matrix, e = i + j*rows (column-major linear index), is word e%4 of the
+ * Philox4x64-10 block (Salmon et al., SC'11) with counter (e/4, 0, 0, 0) and
+ * key (seed, stream_id).  A 64-bit word w becomes u = ((w >> 11) + 0.5) 2^-53
+ * in (0,1); Box-Muller turns words (0,1) and (2,3) of a block into
+ * sqrt(-2 ln u0) cos(2 pi u1), sqrt(-2 ln u0) sin(2 pi u1), and likewise.
+ * purl_urv_factor draws G with stream_id 0.
+ */
+int purl_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double *G, int ldg,
+                  cudaStream_t stream);
+
+/*
+ * purl_qr -- unpivoted Householder QR with diag(R) >= 0 (the building block
+ * of Eqs. (5) and (6)): M = Q R, M m x n (m >= n), Q m x n with orthonormal
+ * columns, R n x n upper triangular.  M is not modified.  Either Q or R may
+ * be NULL.  Blocked compact-WY algorithm; `mode` selects FP64 or the mixed
+ * precision of PURL_MODE_MIXED_BF16 for trailing updates and Q formation.
+ * Workspace as for purl_urv_factor_ex (purl_qr_workspace_bytes).
+ */
+int purl_qr(int m, int n, const double *M, int ldm, double *Q, int ldq, double *R, int ldr,
+            int mode, void *workspace, size_t workspace_bytes, cudaStream_t stream);
+size_t purl_qr_workspace_bytes(int m, int n, int mode);
+
+/*
+ * purl_gemm_f64 -- C = alpha op(A) op(B) + beta C in FP64 (the level-3 product
+ * the paper's Section 3 relies on), op = 'N' or 'T'.  C is m x n, op(A) m x k,
+ * op(B) k x n.  Exposed so the product engine can be tested on its own.
+ */
+int purl_gemm_f64(char transa, char transb, int m, int n, int k, double alpha, const double *A,
+                  int lda, const double *B, int ldb, double beta, double *C, int ldc,
+                  cudaStream_t stream);
+
+/*
+ * purl_urv_truncate -- rank-k approximation of Section 5:
+ *   A_k = U(:,1:k) R(1:k,:) V^T   (m x n, written to Ak, ldak >= m), 0 <= k <= n.
+ * purl_urv_reconstruct is the k = n case (U R V^T).
+ */
+int purl_urv_truncate(int m, int n, int k, const double *U, int ldu, const double *R, int ldr,
+                      const double *V, int ldv, double *Ak, int ldak, cudaStream_t stream);
+int purl_urv_reconstruct(int m, int n, const double *U, int ldu, const double *R, int ldr,
+                         const double *V, int ldv, double *Ak, int ldak, cudaStream_t stream);
+
+/*
+ * purl_device_status -- read and clear the current device's status word
+ * (PURL_OK or the first device-side error since the last call).  Synchronises
+ * `stream`.
+ */
+int purl_device_status(cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PURL_H_ */

@@ -1,0 +1,213 @@
+"""Thin ctypes binding of libpurl (``include/purl.h``); argument marshalling only.
+
+Every function here has the C entry point's name and forwards to it; all
+arithmetic runs in the library's CUDA kernels.  Tensors are torch CUDA
+float64 tensors in column-major layout (``stride(0) == 1``), which is how
+``empty_colmajor`` allocates them; PyTorch provides device memory and the
+current stream, nothing else.  There is no CPU fallback: if ``libpurl.so`` is
+missing or cannot load, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpurl.so")
+
+PURL_OK = 0
+PURL_ERR_SHAPE = -100
+PURL_ERR_NONFINITE = 1
+PURL_ERR_TIMEOUT = 2
+PURL_ERR_CUDA = 3
+PURL_ERR_NOMEM = 4
+PURL_ERR_UNSUPPORTED = 5
+PURL_MODE_FP64 = 0
+PURL_MODE_MIXED_BF16 = 2
+
+# (name, restype, argtypes) for every symbol include/purl.h declares
+_i, _u64, _d, _p, _sz, _c = (ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p,
+                             ctypes.c_size_t, ctypes.c_char)
+SIGNATURES = {
+    "purl_status_str": (ctypes.c_char_p, [_i]),
+    "purl_version": (ctypes.c_char_p, []),
+    "purl_urv_factor": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _p]),
+    "purl_urv_factor_ex": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
+    "purl_urv_workspace_bytes": (_sz, [_i, _i, _i]),
+    "purl_gaussian": (_i, [_u64, _u64, _i, _i, _p, _i, _p]),
+    "purl_qr": (_i, [_i, _i, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
+    "purl_qr_workspace_bytes": (_sz, [_i, _i, _i]),
+    "purl_gemm_f64": (_i, [_c, _c, _i, _i, _i, _d, _p, _i, _p, _i, _d, _p, _i, _p]),
+    "purl_urv_truncate": (_i, [_i, _i, _i, _p, _i, _p, _i, _p, _i, _p, _i, _p]),
+    "purl_urv_reconstruct": (_i, [_i, _i, _p, _i, _p, _i, _p, _i, _p, _i, _p]),
+    "purl_device_status": (_i, [_p]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PurlError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        super().__init__(f"{fn} returned {status}: {status_str(status)}")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpurl.so (built by ``paper_1812_06007_gb300.build``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_1812_06007_gb300.build` (no CPU fallback exists)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_str(status: int) -> str:
+    return lib().purl_status_str(status).decode()
+
+
+def _check(fn: str, status: int):
+    if status != PURL_OK:
+        raise PurlError(fn, status)
+
+
+# ----------------------------------------------------------- tensors ------
+def _torch():
+    import torch
+    return torch
+
+
+def empty_colmajor(rows: int, cols: int, device=None, dtype=None):
+    """Uninitialised rows x cols tensor with column-major strides (1, rows)."""
+    torch = _torch()
+    dtype = dtype or torch.float64
+    return torch.empty((cols, rows), dtype=dtype, device=device or "cuda").t()
+
+
+def as_colmajor(x):
+    """Column-major float64 copy of x on its device (no copy if already so)."""
+    torch = _torch()
+    if x.dtype != torch.float64:
+        x = x.to(torch.float64)
+    if x.dim() != 2:
+        raise ValueError("expected a matrix")
+    if x.numel() == 0 or (x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0])):
+        return x
+    return x.t().contiguous().t()
+
+
+def _ld(x) -> int:
+    if x.numel() == 0:
+        return max(1, x.shape[0])
+    if x.stride(0) != 1 and x.shape[0] > 1:
+        raise ValueError("matrix must be column-major (stride(0) == 1)")
+    return max(int(x.stride(1)), max(1, x.shape[0]))
+
+
+def _cuda_check(*ts):
+    torch = _torch()
+    for t in ts:
+        if t is not None and (not t.is_cuda or t.dtype != torch.float64):
+            raise ValueError("expected CUDA float64 tensors")
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+# ------------------------------------------------------- entry points -----
+def purl_gaussian(seed: int, rows: int, cols: int, stream_id: int = 0, out=None, stream=None):
+    G = out if out is not None else empty_colmajor(rows, cols)
+    _cuda_check(G)
+    _check("purl_gaussian", lib().purl_gaussian(seed, stream_id, rows, cols, _ptr(G), _ld(G), _stream(stream)))
+    return G
+
+
+def purl_urv_factor(A, q: int, reorth: bool, seed: int, mode: int = PURL_MODE_FP64, out=None,
+                    workspace=None, stream=None):
+    """(U, R, V) with A = U R V^T by PowerURV; A is an m x n column-major CUDA float64 tensor."""
+    _cuda_check(A)
+    m, n = A.shape
+    if out is None:
+        U, R, V = empty_colmajor(m, n, A.device), empty_colmajor(n, n, A.device), empty_colmajor(n, n, A.device)
+    else:
+        U, R, V = out
+    _cuda_check(U, R, V)
+    ws_ptr, ws_bytes = (_ptr(workspace), workspace.numel() * workspace.element_size()) if workspace is not None \
+        else (ctypes.c_void_p(0), 0)
+    st = lib().purl_urv_factor_ex(m, n, _ptr(A), _ld(A), q, int(bool(reorth)), seed, _ptr(U), _ld(U), _ptr(R),
+                                  _ld(R), _ptr(V), _ld(V), mode, ws_ptr, ws_bytes, _stream(stream))
+    _check("purl_urv_factor_ex", st)
+    return U, R, V
+
+
+def purl_urv_workspace_bytes(m: int, n: int, mode: int = PURL_MODE_FP64) -> int:
+    return int(lib().purl_urv_workspace_bytes(m, n, mode))
+
+
+def purl_qr(M, mode: int = PURL_MODE_FP64, want_q: bool = True, want_r: bool = True, stream=None):
+    """Q, R with M = Q R, diag(R) >= 0 (unpivoted Householder QR on the GPU)."""
+    _cuda_check(M)
+    m, n = M.shape
+    Q = empty_colmajor(m, n, M.device) if want_q else None
+    R = empty_colmajor(n, n, M.device) if want_r else None
+    st = lib().purl_qr(m, n, _ptr(M), _ld(M), _ptr(Q), _ld(Q) if Q is not None else 1, _ptr(R),
+                       _ld(R) if R is not None else 1, mode, ctypes.c_void_p(0), 0, _stream(stream))
+    _check("purl_qr", st)
+    return Q, R
+
+
+def purl_gemm_f64(transa: str, transb: str, A, B, alpha: float = 1.0, beta: float = 0.0, C=None,
+                  stream=None):
+    _cuda_check(A, B)
+    m = A.shape[0] if transa == "N" else A.shape[1]
+    k = A.shape[1] if transa == "N" else A.shape[0]
+    n = B.shape[1] if transb == "N" else B.shape[0]
+    if C is None:
+        C = empty_colmajor(m, n, A.device)
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs C")
+    _cuda_check(C)
+    st = lib().purl_gemm_f64(transa.encode(), transb.encode(), m, n, k, alpha, _ptr(A), _ld(A), _ptr(B),
+                             _ld(B), beta, _ptr(C), _ld(C), _stream(stream))
+    _check("purl_gemm_f64", st)
+    return C
+
+
+def purl_urv_truncate(U, R, V, k: int, out=None, stream=None):
+    _cuda_check(U, R, V)
+    m, n = U.shape
+    Ak = out if out is not None else empty_colmajor(m, n, U.device)
+    st = lib().purl_urv_truncate(m, n, k, _ptr(U), _ld(U), _ptr(R), _ld(R), _ptr(V), _ld(V), _ptr(Ak),
+                                 _ld(Ak), _stream(stream))
+    _check("purl_urv_truncate", st)
+    return Ak
+
+
+def purl_urv_reconstruct(U, R, V, out=None, stream=None):
+    _cuda_check(U, R, V)
+    m, n = U.shape
+    Ak = out if out is not None else empty_colmajor(m, n, U.device)
+    st = lib().purl_urv_reconstruct(m, n, _ptr(U), _ld(U), _ptr(R), _ld(R), _ptr(V), _ld(V), _ptr(Ak),
+                                    _ld(Ak), _stream(stream))
+    _check("purl_urv_reconstruct", st)
+    return Ak
+
+
+def purl_device_status(stream=None) -> int:
+    return int(lib().purl_device_status(_stream(stream)))

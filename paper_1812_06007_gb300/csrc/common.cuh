@@ -1,0 +1,105 @@
+// common.cuh -- shared internals of libpurl (CUDA, sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "purl.h"
+
+namespace purl {
+
+// ---------------------------------------------------------------- status --
+#define PURL_CUDA_TRY(expr)                                   \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return PURL_ERR_CUDA;              \
+  } while (0)
+
+#define PURL_TRY(expr)                                        \
+  do {                                                        \
+    int _s = (expr);                                          \
+    if (_s != PURL_OK) return _s;                             \
+  } while (0)
+
+// Per-device control block in device memory: the status word that bounded
+// waits write when they give up, and an abort flag that makes the other
+// blocks of the same launch stop waiting too.
+struct DeviceControl {
+  int status;
+  int abort;
+};
+
+struct DeviceInfo {
+  int device = -1;
+  int num_sms = 0;
+  int max_smem_optin = 0;
+  DeviceControl *ctrl = nullptr;  // device pointer
+};
+
+// Lazily initialised per-device info (thread-safe).  Returns nullptr on a
+// CUDA failure.
+const DeviceInfo *device_info();
+
+// Spin budget of a device-side wait: number of polls before giving up
+// (each poll sleeps ~64-128 ns, so this is on the order of a second or more).
+constexpr long long kSpinLimit = 1LL << 24;
+
+// ------------------------------------------------------ grid barrier ------
+// Barrier among the `nblocks` co-resident blocks of a cooperative launch.
+// `counter` starts at 0 for the launch; the i-th barrier (i = 0, 1, ...)
+// completes when the counter reaches (i+1) * nblocks.  Every wait is bounded:
+// on expiry the block records PURL_ERR_TIMEOUT, raises the abort flag and
+// returns false; callers then leave the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target,
+                                             DeviceControl *ctrl) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(counter, 1u);
+    int ok = 1;
+    long long polls = 0;
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+      if (v >= target) break;
+      if (*(volatile int *)&ctrl->abort) { ok = 0; break; }
+      if (++polls > kSpinLimit) {
+        atomicCAS(&ctrl->status, PURL_OK, PURL_ERR_TIMEOUT);
+        atomicExch(&ctrl->abort, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------- helpers -------
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over a workspace.  With base == nullptr it only measures
+// (take() returns nullptr and `used` grows), which is how workspace sizes are
+// computed: the same plan function runs once to size and once to carve.
+struct Arena {
+  char *base = nullptr;
+  size_t size = 0;
+  size_t used = 0;
+  bool ok = true;
+  template <class T>
+  T *take(size_t count) {
+    size_t off = align_up(used, 256);
+    used = off + align_up(count * sizeof(T), 256);
+    if (base == nullptr) return nullptr;
+    if (used > size) { ok = false; return nullptr; }
+    return reinterpret_cast<T *>(base + off);
+  }
+};
+
+}  // namespace purl

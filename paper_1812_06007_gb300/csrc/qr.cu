@@ -1,0 +1,403 @@
+// qr.cu -- blocked unpivoted Householder QR with compact-WY reflectors
+// (Section 2.2: unpivoted QR "can operate on blocks, accumulate Householder
+// reflectors, and then apply the reflectors to the trailing matrix using a
+// level-3 BLAS matrix-matrix multiply").  This is the QR behind Eq. (5), Eq. (6)
+// and every re-orthonormalisation of the power iteration.
+//
+// For each panel of b columns starting at j0:
+//   1. panel_kernel (cooperative, all blocks co-resident): Householder vectors
+//      of the (m-j0) x b panel, one grid barrier per column.  Each block keeps
+//      a slab of rows in shared memory; for column k it publishes, in ONE pass,
+//      the partial sums  sum_{i>k} x_i^2  and  sum_{i>k} x_i a_it  (t > k), so
+//      that after the barrier every block can form beta, tau and the
+//      reflector's action on the remaining panel columns without a second
+//      round trip (v = (x - beta e_k)/v0 is never needed before the barrier).
+//   2. T factor (b x b upper triangular, I - V T V^T = H_0 ... H_{b-1}) from
+//      the Gram matrix V^T V (a split-K product) by the column recurrence
+//      T(0:k,k) = -tau_k T(0:k,0:k) (V(:,0:k)^T v_k).
+//   3. Trailing update C <- (I - V T^T V^T) C as three steps: W = V^T C
+//      (split-K), W <- T^T W, C <- C - V W.
+// The explicit Q is formed afterwards by applying the blocks, last to first,
+// to the first n columns of the identity; the signs are then normalised so
+// that diag(R) >= 0 (the convention of the footnote in Section 2.2 that makes
+// the factorization unique).
+#include "common.cuh"
+#include "qr.cuh"
+
+namespace purl {
+
+int gemm_f64(bool ta, bool tb, int m, int n, int k, double alpha, const double *A, int lda,
+             const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s);
+int gemm_f64_splitk(bool ta, bool tb, int m, int n, int k, int splits, int k_chunk,
+                    const double *A, int lda, const double *B, int ldb, double *P, cudaStream_t s);
+void choose_splits(int m, int n, int k, int num_sms, int *splits, int *k_chunk);
+
+namespace {
+
+constexpr int PNT = 256;  // panel kernel threads
+constexpr int PW = PNT / 32;
+
+// ------------------------------------------------------------ panel -------
+// F points at F(j0, j0); the panel has `rows` rows and `bw` <= QR_B columns.
+// Block c owns panel rows [c*ch, min(rows, (c+1)*ch)).
+__global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, double *F,
+                                                    long long ldf, double *Vb, long long ldv,
+                                                    double *tau, double *part, double *rowk,
+                                                    unsigned *counter, DeviceControl *ctrl) {
+  extern __shared__ double Ps[];  // ch x QR_B, column-major (column t at Ps + t*ch)
+  __shared__ double s_w[QR_B];
+  __shared__ double s_par[3];     // beta, v0, tau
+  const int P = gridDim.x;
+  const int c = blockIdx.x;
+  const int r0 = c * ch;
+  const int nr = max(0, min(rows, r0 + ch) - r0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int e = tid; e < ch * bw; e += PNT) {
+    int i = e % ch, t = e / ch;
+    Ps[t * ch + i] = (i < nr) ? F[(r0 + i) + t * ldf] : 0.0;
+  }
+  __syncthreads();
+
+  for (int k = 0; k < bw; ++k) {
+    const int buf = k & 1;
+    double *pb = part + (size_t)buf * P * QR_B;
+    double *rk = rowk + (size_t)buf * QR_B;
+    // rows of this block strictly below row k
+    const int i_lo = max(0, k + 1 - r0);
+    // (a) partials: t == k gives sum x_i^2, t > k gives sum x_i a_it
+    for (int t = k + warp; t < bw; t += PW) {
+      double s = 0.0;
+      for (int i = i_lo + lane; i < nr; i += 32) s += Ps[k * ch + i] * Ps[t * ch + i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) __stcg(&pb[(size_t)c * QR_B + t], s);
+    }
+    if (k >= r0 && k < r0 + nr)
+      for (int t = k + tid; t < bw; t += PNT) __stcg(&rk[t], Ps[t * ch + (k - r0)]);
+    // (b) one barrier per column
+    if (!grid_barrier(counter, (unsigned)(k + 1) * P, ctrl)) return;
+    // (c) every block reduces the partials in the same fixed order
+    for (int t = k + warp; t < bw; t += PW) {
+      double s = 0.0;
+      for (int b = lane; b < P; b += 32) s += __ldcg(&pb[(size_t)b * QR_B + t]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) s_w[t] = s;  // s_w[k] = sigma, s_w[t>k] = dot_t
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double sigma = s_w[k];
+      double x0 = __ldcg(&rk[k]);
+      if (sigma == 0.0) {
+        s_par[0] = x0; s_par[1] = 1.0; s_par[2] = 0.0;
+      } else {
+        double norm = sqrt(x0 * x0 + sigma);
+        double beta = (x0 >= 0.0) ? -norm : norm;
+        s_par[0] = beta; s_par[1] = x0 - beta; s_par[2] = (beta - x0) / beta;
+      }
+      if (c == 0) tau[k] = s_par[2];
+    }
+    __syncthreads();
+    const double beta = s_par[0], v0 = s_par[1], tk = s_par[2];
+    if (tk != 0.0) {
+      // w_t = tau (a_kt + v(k+1:)^T a_t) with v(k+1:) = x(k+1:)/v0
+      for (int t = k + 1 + tid; t < bw; t += PNT) s_w[t] = tk * (__ldcg(&rk[t]) + s_w[t] / v0);
+      for (int i = i_lo + tid; i < nr; i += PNT) Ps[k * ch + i] /= v0;
+      __syncthreads();
+      if (k >= r0 && k < r0 + nr && tid == 0) Ps[k * ch + (k - r0)] = beta;
+      const int ncol = bw - k - 1;
+      const int i_from = max(0, k - r0);  // include row k itself (v_k = 1)
+      const int span = nr - i_from;
+      if (ncol > 0 && span > 0) {
+        for (int e = tid; e < ncol * span; e += PNT) {
+          int t = k + 1 + e / span, i = i_from + e % span;
+          double v = (r0 + i == k) ? 1.0 : Ps[k * ch + i];
+          Ps[t * ch + i] -= s_w[t] * v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  for (int e = tid; e < nr * bw; e += PNT) {
+    int i = e % nr, t = e / nr;
+    int gi = r0 + i;
+    double x = Ps[t * ch + i];
+    F[gi + t * ldf] = x;
+    Vb[gi + t * ldv] = (gi < t) ? 0.0 : (gi == t ? 1.0 : x);
+  }
+}
+
+// ------------------------------------------------------------ T factor ----
+// Sum the split-K partials of the Gram matrix V^T V and run the forward
+// column recurrence of the compact-WY T factor.  One block.
+__global__ void __launch_bounds__(256) larft_kernel(int bw, int splits, const double *Gp,
+                                                    const double *tau, double *T) {
+  __shared__ double Gm[QR_B][QR_B + 1];
+  __shared__ double Ts[QR_B][QR_B + 1];
+  for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) {
+    int i = e % bw, j = e / bw;
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += Gp[(size_t)z * bw * bw + e];
+    Gm[i][j] = s;
+    Ts[i][j] = 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < bw; ++k) {
+    double tk = tau[k];
+    int i = threadIdx.x;
+    double s = 0.0;
+    if (i < k)
+      for (int l = i; l < k; ++l) s += Ts[i][l] * Gm[l][k];
+    __syncthreads();
+    if (i < k) Ts[i][k] = -tk * s;
+    if (i == k) Ts[k][k] = tk;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < QR_B * QR_B; e += blockDim.x) {
+    int i = e % QR_B, j = e / QR_B;
+    T[e] = (i < bw && j < bw) ? Ts[i][j] : 0.0;
+  }
+}
+
+// W2(:, c) = op(T) * sum_z Wp_z(:, c); op(T) = T^T when trans, else T.
+// Block handles 32 columns; T kept in shared memory.
+__global__ void __launch_bounds__(256) reduce_tmul_kernel(int bw, int nc, int splits,
+                                                          const double *Wp, const double *T,
+                                                          bool trans, double *W2) {
+  __shared__ double Ts[QR_B][QR_B + 1];
+  __shared__ double Ws[32][QR_B + 1];
+  const int c0 = blockIdx.x * 32;
+  for (int e = threadIdx.x; e < QR_B * QR_B; e += blockDim.x) {
+    int i = e % QR_B, j = e / QR_B;
+    Ts[i][j] = trans ? T[j + i * QR_B] : T[e];  // Ts = op(T)
+  }
+  for (int e = threadIdx.x; e < 32 * bw; e += blockDim.x) {
+    int r = e % bw, cc = e / bw;
+    int col = c0 + cc;
+    double s = 0.0;
+    if (col < nc)
+      for (int z = 0; z < splits; ++z) s += Wp[(size_t)z * bw * nc + r + (size_t)col * bw];
+    Ws[cc][r] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * bw; e += blockDim.x) {
+    int r = e % bw, cc = e / bw;
+    int col = c0 + cc;
+    if (col >= nc) continue;
+    double s = 0.0;
+    for (int l = 0; l < bw; ++l) s += Ts[r][l] * Ws[cc][l];
+    W2[r + (size_t)col * bw] = s;
+  }
+}
+
+// Vb = explicit unit-lower-trapezoidal V of the panel at F(j0, j0).
+__global__ void extract_v_kernel(int rows, int bw, const double *F, long long ldf, double *Vb,
+                                 long long ldv) {
+  long long total = (long long)rows * bw;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e % rows), t = (int)(e / rows);
+    Vb[i + t * ldv] = (i < t) ? 0.0 : (i == t ? 1.0 : F[i + t * ldf]);
+  }
+}
+
+__global__ void set_identity_kernel(int m, int n, double *Q, long long ldq) {
+  long long total = (long long)m * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e % m), j = (int)(e / m);
+    Q[i + j * ldq] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+// diag(R) >= 0: flip column j of Q and row j of R where F(j,j) < 0; R gets
+// zeros below the diagonal.
+__global__ void sign_fix_kernel(int m, int n, const double *F, long long ldf, double *Q,
+                                long long ldq, double *R, long long ldr) {
+  long long totq = Q ? (long long)m * n : 0;
+  long long totr = R ? (long long)n * n : 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < totq + totr;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < totq) {
+      int i = (int)(e % m), j = (int)(e / m);
+      if (F[j + j * ldf] < 0.0) Q[i + j * ldq] = -Q[i + j * ldq];
+    } else {
+      long long f = e - totq;
+      int i = (int)(f % n), j = (int)(f / n);
+      double v = 0.0;
+      if (i <= j) {
+        v = F[i + j * ldf];
+        if (F[i + i * ldf] < 0.0) v = -v;
+      }
+      R[i + j * ldr] = v;
+    }
+  }
+}
+
+__global__ void copy_kernel(int m, int n, const double *X, long long ldx, double *Y,
+                            long long ldy) {
+  long long total = (long long)m * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e % m), j = (int)(e / m);
+    Y[i + j * ldy] = X[i + j * ldx];
+  }
+}
+
+int grid_for(long long total, const DeviceInfo *di) {
+  long long g = (total + 255) / 256;
+  long long cap = (long long)di->num_sms * 16;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// Max co-resident blocks for a panel launch with `smem` dynamic bytes.
+int panel_capacity(const DeviceInfo *di, size_t smem) {
+  static thread_local int cached_dev = -1;
+  static thread_local size_t cached_smem = 0;
+  static thread_local int cached_cap = 0;
+  if (cached_dev == di->device && cached_smem == smem) return cached_cap;
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, PNT, smem) !=
+      cudaSuccess)
+    return 0;
+  cached_dev = di->device;
+  cached_smem = smem;
+  cached_cap = per_sm * di->num_sms;
+  return cached_cap;
+}
+
+}  // namespace
+
+int panel_blocks(int rows, const DeviceInfo *di) {
+  int P = ceil_div(rows, 64);
+  if (P > di->num_sms) P = di->num_sms;
+  return P < 1 ? 1 : P;
+}
+
+int qr_plan(Arena &ar, int m, int n, int mode, QrWork *w) {
+  (void)mode;
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  int npan = ceil_div(n, QR_B);
+  w->tau = ar.take<double>(n > 0 ? n : 1);
+  w->T = ar.take<double>((size_t)(npan > 0 ? npan : 1) * QR_B * QR_B);
+  w->Vb = ar.take<double>((size_t)(m > 0 ? m : 1) * QR_B);
+  w->Wp = ar.take<double>((size_t)QR_MAX_SPLITS * QR_B * (n > 0 ? n : 1));
+  w->W2 = ar.take<double>((size_t)QR_B * (n > 0 ? n : 1));
+  w->Gp = ar.take<double>((size_t)QR_MAX_SPLITS * QR_B * QR_B);
+  w->part = ar.take<double>((size_t)2 * di->num_sms * QR_B);
+  w->rowk = ar.take<double>(2 * QR_B);
+  w->counters = ar.take<unsigned>(npan > 0 ? npan : 1);
+  return PURL_OK;
+}
+
+// Apply the block reflector of one panel (V in w.Vb, T) to C (rows x nc):
+// C <- (I - V op(T) V^T) C with op(T) = T^T (trans, i.e. Q^T C) or T.
+static int apply_block(int rows, int bw, int nc, double *C, int ldc, const double *T, bool trans,
+                       QrWork &w, const DeviceInfo *di, cudaStream_t s) {
+  if (nc <= 0 || rows <= 0 || bw <= 0) return PURL_OK;
+  int splits, chunk;
+  choose_splits(bw, nc, rows, di->num_sms, &splits, &chunk);
+  PURL_TRY(gemm_f64_splitk(true, false, bw, nc, rows, splits, chunk, w.Vb, rows, C, ldc, w.Wp, s));
+  reduce_tmul_kernel<<<ceil_div(nc, 32), 256, 0, s>>>(bw, nc, splits, w.Wp, T, trans, w.W2);
+  PURL_CUDA_TRY(cudaGetLastError());
+  return gemm_f64(false, false, rows, nc, bw, -1.0, w.Vb, rows, w.W2, bw, 1.0, C, ldc, s);
+}
+
+int qr_factor_f64(int m, int n, double *F, int ldf, QrWork &w, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  if (n == 0) return PURL_OK;
+  int npan = ceil_div(n, QR_B);
+  PURL_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * npan, s));
+  for (int p = 0; p < npan; ++p) {
+    int j0 = p * QR_B;
+    int bw = min(QR_B, n - j0);
+    int rows = m - j0;
+    double *Fp = F + j0 + (size_t)j0 * ldf;
+    int P = panel_blocks(rows, di);
+    int ch = ceil_div(rows, P);
+    size_t smem = (size_t)ch * QR_B * sizeof(double);
+    if (smem > (size_t)di->max_smem_optin - 4096) return PURL_ERR_UNSUPPORTED;
+    int cap = panel_capacity(di, smem);
+    if (cap < P) return PURL_ERR_UNSUPPORTED;
+    double *taup = w.tau + j0;
+    unsigned *cnt = w.counters + p;
+    int ldv = rows;
+    long long ldf_ll = ldf, ldv_ll = ldv;
+    void *args[] = {&rows, &bw, &ch, &Fp, &ldf_ll, &w.Vb, &ldv_ll, &taup, &w.part, &w.rowk, &cnt,
+                    (void *)&di->ctrl};
+    PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel, dim3(P), dim3(PNT), args,
+                                              smem, s));
+    // T factor from the Gram matrix V^T V
+    int gs, gchunk;
+    choose_splits(bw, bw, rows, di->num_sms, &gs, &gchunk);
+    if (gs > QR_MAX_SPLITS) gs = QR_MAX_SPLITS, gchunk = ceil_div(ceil_div(rows, gs), 16) * 16;
+    PURL_TRY(gemm_f64_splitk(true, false, bw, bw, rows, gs, gchunk, w.Vb, ldv, w.Vb, ldv, w.Gp, s));
+    double *Tp = w.T + (size_t)p * QR_B * QR_B;
+    larft_kernel<<<1, 256, 0, s>>>(bw, gs, w.Gp, taup, Tp);
+    PURL_CUDA_TRY(cudaGetLastError());
+    // trailing update with Q_p^T
+    PURL_TRY(apply_block(rows, bw, n - j0 - bw, Fp + (size_t)bw * ldf, ldf, Tp, true, w, di, s));
+  }
+  return PURL_OK;
+}
+
+int qr_form_q_f64(int m, int n, const double *F, int ldf, QrWork &w, double *Q, int ldq,
+                  cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  if (m == 0 || n == 0) return PURL_OK;
+  set_identity_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, Q, ldq);
+  PURL_CUDA_TRY(cudaGetLastError());
+  int npan = ceil_div(n, QR_B);
+  for (int p = npan - 1; p >= 0; --p) {
+    int j0 = p * QR_B;
+    int bw = min(QR_B, n - j0);
+    int rows = m - j0;
+    extract_v_kernel<<<grid_for((long long)rows * bw, di), 256, 0, s>>>(
+        rows, bw, F + j0 + (size_t)j0 * ldf, ldf, w.Vb, rows);
+    PURL_CUDA_TRY(cudaGetLastError());
+    const double *Tp = w.T + (size_t)p * QR_B * QR_B;
+    PURL_TRY(apply_block(rows, bw, n - j0, Q + j0 + (size_t)j0 * ldq, ldq, Tp, false, w, di, s));
+  }
+  return PURL_OK;
+}
+
+int qr_sign_fix(int m, int n, const double *F, int ldf, double *Q, int ldq, double *R, int ldr,
+                cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  long long tot = (Q ? (long long)m * n : 0) + (R ? (long long)n * n : 0);
+  if (tot == 0) return PURL_OK;
+  sign_fix_kernel<<<grid_for(tot, di), 256, 0, s>>>(m, n, F, ldf, Q, ldq, R, ldr);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+int copy_matrix(int m, int n, const double *X, int ldx, double *Y, int ldy, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  if ((long long)m * n == 0) return PURL_OK;
+  copy_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, X, ldx, Y, ldy);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+// Full QR with explicit Q and diag(R) >= 0: F holds M on entry (m x n, ld
+// ldf) and the packed factor on exit.
+int qr_explicit(int m, int n, double *F, int ldf, double *Q, int ldq, double *R, int ldr,
+                int mode, QrWork &w, cudaStream_t s) {
+  (void)mode;
+  PURL_TRY(qr_factor_f64(m, n, F, ldf, w, s));
+  if (Q) PURL_TRY(qr_form_q_f64(m, n, F, ldf, w, Q, ldq, s));
+  return qr_sign_fix(m, n, F, ldf, Q, ldq, R, ldr, s);
+}
+
+}  // namespace purl

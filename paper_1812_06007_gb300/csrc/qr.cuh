@@ -1,0 +1,33 @@
+// qr.cuh -- internal interface of the blocked Householder QR engine.
+#pragma once
+
+#include "common.cuh"
+
+namespace purl {
+
+constexpr int QR_B = 32;            // panel width (columns per compact-WY block)
+constexpr int QR_MAX_SPLITS = 64;   // split-K partial buffers for V^T C
+
+struct QrWork {
+  double *tau = nullptr;       // n reflector scalars
+  double *T = nullptr;         // ceil(n/QR_B) blocks of QR_B x QR_B
+  double *Vb = nullptr;        // explicit V of the current panel, m x QR_B
+  double *Wp = nullptr;        // split-K partials of V^T C
+  double *W2 = nullptr;        // op(T) V^T C, QR_B x n
+  double *Gp = nullptr;        // split-K partials of V^T V
+  double *part = nullptr;      // panel kernel: per-block partial sums (2 buffers)
+  double *rowk = nullptr;      // panel kernel: pivot-row values (2 buffers)
+  unsigned *counters = nullptr;  // one grid-barrier counter per panel
+};
+
+int qr_plan(Arena &ar, int m, int n, int mode, QrWork *w);
+int qr_factor_f64(int m, int n, double *F, int ldf, QrWork &w, cudaStream_t s);
+int qr_form_q_f64(int m, int n, const double *F, int ldf, QrWork &w, double *Q, int ldq,
+                  cudaStream_t s);
+int qr_sign_fix(int m, int n, const double *F, int ldf, double *Q, int ldq, double *R, int ldr,
+                cudaStream_t s);
+int qr_explicit(int m, int n, double *F, int ldf, double *Q, int ldq, double *R, int ldr,
+                int mode, QrWork &w, cudaStream_t s);
+int copy_matrix(int m, int n, const double *X, int ldx, double *Y, int ldy, cudaStream_t s);
+
+}  // namespace purl

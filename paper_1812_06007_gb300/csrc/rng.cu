@@ -1,0 +1,72 @@
+// rng.cu -- the Gaussian start matrix G of PowerURV (Section 3: "a Gaussian
+// random matrix G in R^{n x n} is drawn").  The paper names no generator;
+// this library uses the counter-based Philox4x64-10 (Salmon, Moraes, Dror,
+// Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11) so that every
+// element is a pure function of (seed, stream, position) and the draw is
+// embarrassingly parallel, then Box-Muller for the normal deviates.
+#include "common.cuh"
+
+namespace purl {
+
+namespace {
+
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += W0; k1 += W1;  // the bump after the last round is unused
+  }
+}
+
+__device__ __forceinline__ double u53(uint64_t x) {
+  return (static_cast<double>(x >> 11) + 0.5) * 0x1.0p-53;
+}
+
+// One thread per Philox block: 4 consecutive (column-major) elements.
+__global__ void __launch_bounds__(256) gaussian_kernel(uint64_t seed, uint64_t stream_id,
+                                                       int rows, long long count, double *G,
+                                                       long long ldg) {
+  const double two_pi = 6.283185307179586476925286766559;
+  long long nblk = (count + 3) / 4;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nblk;
+       b += (long long)gridDim.x * blockDim.x) {
+    uint64_t c[4] = {static_cast<uint64_t>(b), 0, 0, 0};
+    philox4x64_10(c, seed, stream_id);
+    double z[4];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      double r = sqrt(-2.0 * log(u53(c[2 * p])));
+      double s, co;
+      sincos(two_pi * u53(c[2 * p + 1]), &s, &co);
+      z[2 * p] = r * co;
+      z[2 * p + 1] = r * s;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      long long e = 4 * b + t;
+      if (e < count) G[(e % rows) + (e / rows) * ldg] = z[t];
+    }
+  }
+}
+
+}  // namespace
+
+int launch_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double *G, int ldg,
+                    cudaStream_t stream) {
+  long long count = (long long)rows * cols;
+  if (count == 0) return PURL_OK;
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  long long nblk = (count + 3) / 4;
+  long long want = (nblk + 255) / 256;
+  int grid = (int)(want < (long long)di->num_sms * 8 ? want : (long long)di->num_sms * 8);
+  gaussian_kernel<<<grid, 256, 0, stream>>>(seed, stream_id, rows, count, G, ldg);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+}  // namespace purl

@@ -1,0 +1,296 @@
+// urv.cu -- the PowerURV driver (Section 3) and the C ABI of libpurl.
+//
+//   Y = G;  for i = 1..q:  Z = A Y      [Z <- Q(Z)  if reorth]
+//                          Y = A^T Z    [Y <- Q(Y)  if reorth and i < q]
+//   Eq. (5):  Y = V Z'  (Householder QR, diag(Z') >= 0)
+//   Eq. (6):  A V = U R (Householder QR, diag(R) >= 0)
+//
+// The last power iterate needs no separate re-orthonormalisation: the QR of
+// Eq. (5) is it.  q = 0 is DDH-URV (Section 2.2).  Everything is enqueued on
+// the caller's stream; nothing synchronises.
+#include <mutex>
+
+#include "common.cuh"
+#include "qr.cuh"
+
+namespace purl {
+
+int launch_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double *G, int ldg,
+                    cudaStream_t stream);
+int gemm_f64(bool ta, bool tb, int m, int n, int k, double alpha, const double *A, int lda,
+             const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s);
+
+// ------------------------------------------------------------ devices -----
+const DeviceInfo *device_info() {
+  static std::mutex mu;
+  static DeviceInfo infos[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  DeviceInfo &di = infos[dev];
+  if (di.device == dev) return &di;
+  int sms = 0, smem = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return nullptr;
+  if (cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return nullptr;
+  DeviceControl *ctrl = nullptr;
+  if (cudaMalloc(&ctrl, sizeof(DeviceControl)) != cudaSuccess) return nullptr;
+  if (cudaMemset(ctrl, 0, sizeof(DeviceControl)) != cudaSuccess) return nullptr;
+  if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
+  di.num_sms = sms;
+  di.max_smem_optin = smem;
+  di.ctrl = ctrl;
+  di.device = dev;
+  return &di;
+}
+
+// --------------------------------------------------------- workspace ------
+struct UrvWork {
+  double *buf[3] = {nullptr, nullptr, nullptr};  // each m x n
+  QrWork qr;
+};
+
+static int urv_plan(Arena &ar, int m, int n, int mode, UrvWork *w) {
+  size_t mn = (size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1);
+  for (int i = 0; i < 3; ++i) w->buf[i] = ar.take<double>(mn);
+  return qr_plan(ar, m, n, mode, &w->qr);
+}
+
+static bool mode_ok(int mode) { return mode == PURL_MODE_FP64; }
+
+// Stream-ordered scratch: the caller's workspace, or one allocated on the stream.
+struct Scratch {
+  void *ptr = nullptr;
+  bool owned = false;
+  cudaStream_t s = 0;
+  int acquire(void *ws, size_t ws_bytes, size_t need, cudaStream_t stream) {
+    s = stream;
+    if (ws) {
+      if (ws_bytes < need) return PURL_ERR_NOMEM;
+      ptr = ws;
+      return PURL_OK;
+    }
+    if (need == 0) return PURL_OK;
+    if (cudaMallocAsync(&ptr, need, stream) != cudaSuccess) return PURL_ERR_NOMEM;
+    owned = true;
+    return PURL_OK;
+  }
+  ~Scratch() {
+    if (owned) cudaFreeAsync(ptr, s);
+  }
+};
+
+static int urv_run(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                   double *U, int ldu, double *R, int ldr, double *V, int ldv, int mode,
+                   UrvWork &w, cudaStream_t s) {
+  double *Y = w.buf[0], *Z = w.buf[1], *F = w.buf[2];
+  PURL_TRY(launch_gaussian(seed, 0, n, n, Y, n, s));
+  for (int i = 1; i <= q; ++i) {
+    PURL_TRY(gemm_f64(false, false, m, n, n, 1.0, A, lda, Y, n, 0.0, F, m, s));  // F = A Y
+    if (reorth) {
+      PURL_TRY(qr_factor_f64(m, n, F, m, w.qr, s));
+      PURL_TRY(qr_form_q_f64(m, n, F, m, w.qr, Z, m, s));
+      PURL_TRY(qr_sign_fix(m, n, F, m, Z, m, nullptr, 0, s));
+    } else {
+      double *t = F; F = Z; Z = t;
+    }
+    PURL_TRY(gemm_f64(true, false, n, n, m, 1.0, A, lda, Z, m, 0.0, F, n, s));  // F = A^T Z
+    if (reorth && i < q) {
+      PURL_TRY(qr_factor_f64(n, n, F, n, w.qr, s));
+      PURL_TRY(qr_form_q_f64(n, n, F, n, w.qr, Y, n, s));
+      PURL_TRY(qr_sign_fix(n, n, F, n, Y, n, nullptr, 0, s));
+    } else {
+      double *t = F; F = Y; Y = t;
+    }
+  }
+  // Eq. (5): (A^T A)^q G = V Z'
+  PURL_TRY(qr_factor_f64(n, n, Y, n, w.qr, s));
+  PURL_TRY(qr_form_q_f64(n, n, Y, n, w.qr, V, ldv, s));
+  PURL_TRY(qr_sign_fix(n, n, Y, n, V, ldv, nullptr, 0, s));
+  // Eq. (6): A V = U R
+  PURL_TRY(gemm_f64(false, false, m, n, n, 1.0, A, lda, V, ldv, 0.0, F, m, s));
+  PURL_TRY(qr_factor_f64(m, n, F, m, w.qr, s));
+  PURL_TRY(qr_form_q_f64(m, n, F, m, w.qr, U, ldu, s));
+  return qr_sign_fix(m, n, F, m, U, ldu, R, ldr, s);
+}
+
+static int check_factor_args(int m, int n, const double *A, int lda, int q, double *U, int ldu,
+                             double *R, int ldr, double *V, int ldv) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (m < n) return PURL_ERR_SHAPE;
+  if (!A && (long long)m * n > 0) return -3;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  if (q < 0) return -5;
+  if (!U && (long long)m * n > 0) return -8;
+  if (ldu < (m > 1 ? m : 1)) return -9;
+  if (!R && n > 0) return -10;
+  if (ldr < (n > 1 ? n : 1)) return -11;
+  if (!V && n > 0) return -12;
+  if (ldv < (n > 1 ? n : 1)) return -13;
+  return PURL_OK;
+}
+
+}  // namespace purl
+
+using namespace purl;
+
+extern "C" {
+
+const char *purl_status_str(int status) {
+  switch (status) {
+    case PURL_OK: return "ok";
+    case PURL_ERR_SHAPE: return "m < n: factor the transpose instead";
+    case PURL_ERR_NONFINITE: return "non-finite input";
+    case PURL_ERR_TIMEOUT: return "a bounded device-side wait ran out";
+    case PURL_ERR_CUDA: return "CUDA runtime error";
+    case PURL_ERR_NOMEM: return "workspace allocation failed or too small";
+    case PURL_ERR_UNSUPPORTED: return "unsupported on this device or build";
+    default: return status < 0 ? "invalid argument (-i = i-th argument)" : "unknown status";
+  }
+}
+
+const char *purl_version(void) { return "purl 0.1.0 sm_103a"; }
+
+size_t purl_urv_workspace_bytes(int m, int n, int mode) {
+  if (m < 0 || n < 0 || m < n || !mode_ok(mode)) return 0;
+  Arena ar;
+  UrvWork w;
+  if (urv_plan(ar, m, n, mode, &w) != PURL_OK) return 0;
+  return ar.used;
+}
+
+int purl_urv_factor_ex(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                       double *U, int ldu, double *R, int ldr, double *V, int ldv, int mode,
+                       void *workspace, size_t workspace_bytes, cudaStream_t stream) {
+  int st = check_factor_args(m, n, A, lda, q, U, ldu, R, ldr, V, ldv);
+  if (st != PURL_OK) return st;
+  if (!mode_ok(mode)) return -14;
+  if (n == 0) return PURL_OK;
+  if (!device_info()) return PURL_ERR_CUDA;
+  size_t need = purl_urv_workspace_bytes(m, n, mode);
+  Scratch scratch;
+  PURL_TRY(scratch.acquire(workspace, workspace_bytes, need, stream));
+  Arena ar;
+  ar.base = static_cast<char *>(scratch.ptr);
+  ar.size = workspace ? workspace_bytes : need;
+  UrvWork w;
+  PURL_TRY(urv_plan(ar, m, n, mode, &w));
+  if (!ar.ok) return PURL_ERR_NOMEM;
+  return urv_run(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, mode, w, stream);
+}
+
+int purl_urv_factor(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                    double *U, int ldu, double *R, int ldr, double *V, int ldv,
+                    cudaStream_t stream) {
+  return purl_urv_factor_ex(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, PURL_MODE_FP64,
+                            nullptr, 0, stream);
+}
+
+int purl_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double *G, int ldg,
+                  cudaStream_t stream) {
+  if (rows < 0) return -3;
+  if (cols < 0) return -4;
+  if (!G && (long long)rows * cols > 0) return -5;
+  if (ldg < (rows > 1 ? rows : 1)) return -6;
+  return launch_gaussian(seed, stream_id, rows, cols, G, ldg, stream);
+}
+
+size_t purl_qr_workspace_bytes(int m, int n, int mode) {
+  if (m < 0 || n < 0 || m < n || !mode_ok(mode)) return 0;
+  Arena ar;
+  double *F = ar.take<double>((size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1));
+  (void)F;
+  QrWork w;
+  if (qr_plan(ar, m, n, mode, &w) != PURL_OK) return 0;
+  return ar.used;
+}
+
+int purl_qr(int m, int n, const double *M, int ldm, double *Q, int ldq, double *R, int ldr,
+            int mode, void *workspace, size_t workspace_bytes, cudaStream_t stream) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (m < n) return PURL_ERR_SHAPE;
+  if (!M && (long long)m * n > 0) return -3;
+  if (ldm < (m > 1 ? m : 1)) return -4;
+  if (Q && ldq < (m > 1 ? m : 1)) return -6;
+  if (R && ldr < (n > 1 ? n : 1)) return -8;
+  if (!mode_ok(mode)) return -9;
+  if (n == 0) return PURL_OK;
+  if (!device_info()) return PURL_ERR_CUDA;
+  size_t need = purl_qr_workspace_bytes(m, n, mode);
+  Scratch scratch;
+  PURL_TRY(scratch.acquire(workspace, workspace_bytes, need, stream));
+  Arena ar;
+  ar.base = static_cast<char *>(scratch.ptr);
+  ar.size = workspace ? workspace_bytes : need;
+  double *F = ar.take<double>((size_t)m * n);
+  QrWork w;
+  PURL_TRY(qr_plan(ar, m, n, mode, &w));
+  if (!ar.ok) return PURL_ERR_NOMEM;
+  PURL_TRY(copy_matrix(m, n, M, ldm, F, m, stream));
+  return qr_explicit(m, n, F, m, Q, ldq, R, ldr, mode, w, stream);
+}
+
+int purl_gemm_f64(char transa, char transb, int m, int n, int k, double alpha, const double *A,
+                  int lda, const double *B, int ldb, double beta, double *C, int ldc,
+                  cudaStream_t stream) {
+  bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
+  if (!ta && transa != 'N' && transa != 'n') return -1;
+  if (!tb && transb != 'N' && transb != 'n') return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  int arows = ta ? k : m, brows = tb ? n : k;
+  if (!A && (long long)m * k > 0) return -7;
+  if (lda < (arows > 1 ? arows : 1)) return -8;
+  if (!B && (long long)k * n > 0) return -9;
+  if (ldb < (brows > 1 ? brows : 1)) return -10;
+  if (!C && (long long)m * n > 0) return -12;
+  if (ldc < (m > 1 ? m : 1)) return -13;
+  if (!device_info()) return PURL_ERR_CUDA;
+  return gemm_f64(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+}
+
+int purl_urv_truncate(int m, int n, int k, const double *U, int ldu, const double *R, int ldr,
+                      const double *V, int ldv, double *Ak, int ldak, cudaStream_t stream) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (m < n) return PURL_ERR_SHAPE;
+  if (k < 0 || k > n) return -3;
+  if (!U && (long long)m * n > 0) return -4;
+  if (ldu < (m > 1 ? m : 1)) return -5;
+  if (!R && n > 0) return -6;
+  if (ldr < (n > 1 ? n : 1)) return -7;
+  if (!V && n > 0) return -8;
+  if (ldv < (n > 1 ? n : 1)) return -9;
+  if (!Ak && (long long)m * n > 0) return -10;
+  if (ldak < (m > 1 ? m : 1)) return -11;
+  if ((long long)m * n == 0) return PURL_OK;
+  if (!device_info()) return PURL_ERR_CUDA;
+  if (k == 0) return gemm_f64(false, false, m, n, 0, 0.0, U, ldu, R, ldr, 0.0, Ak, ldak, stream);
+  Scratch scratch;
+  PURL_TRY(scratch.acquire(nullptr, 0, sizeof(double) * (size_t)k * n, stream));
+  double *W = static_cast<double *>(scratch.ptr);
+  // W = R(1:k, :) V^T  (k x n), then A_k = U(:, 1:k) W
+  PURL_TRY(gemm_f64(false, true, k, n, n, 1.0, R, ldr, V, ldv, 0.0, W, k, stream));
+  return gemm_f64(false, false, m, n, k, 1.0, U, ldu, W, k, 0.0, Ak, ldak, stream);
+}
+
+int purl_urv_reconstruct(int m, int n, const double *U, int ldu, const double *R, int ldr,
+                         const double *V, int ldv, double *Ak, int ldak, cudaStream_t stream) {
+  return purl_urv_truncate(m, n, n, U, ldu, R, ldr, V, ldv, Ak, ldak, stream);
+}
+
+int purl_device_status(cudaStream_t stream) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return PURL_ERR_CUDA;
+  DeviceControl h{};
+  if (cudaMemcpy(&h, di->ctrl, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return PURL_ERR_CUDA;
+  DeviceControl z{};
+  if (cudaMemcpy(di->ctrl, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return PURL_ERR_CUDA;
+  return h.status;
+}
+
+}  // extern "C"
