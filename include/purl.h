@@ -127,6 +127,27 @@ int purl_gemm_f64(char transa, char transb, int m, int n, int k, double alpha, c
                   cudaStream_t stream);
 
 /*
+ * purl_gemm_tc -- the same product on the BF16 tensor cores (tcgen05, FP32
+ * accumulation in tensor memory) with `slices` in {1, 2, 3}: each FP64
+ * operand is split into that many BF16 slices and the slice pairs (s, t) with
+ * s + t < slices are multiplied (1, 3 or 6 BF16 products).
+ *   exact = 0: floating slices X_0 = bf16(X), X_1 = bf16(X - X_0), ...; the
+ *              accumulator's own rounding limits the result to about
+ *              (k/16) 2^-23 of sum |a||b| however many slices are used.
+ *   exact = 1: Ozaki-style fixed-point slices (a power-of-two scale per row
+ *              of op(A) and per column of op(B), slices are integers of at
+ *              most 8 bits) whose products sum without any rounding in the
+ *              FP32 accumulator; the tensor memory is drained into
+ *              double-FP32 sums every 256 of k.  Error about 2^(-8 slices)
+ *              of (row scale) x (column scale) x k.
+ * This is the product engine of the mixed-precision mode.  Operand slices are
+ * staged in scratch allocated on `stream`.
+ */
+int purl_gemm_tc(char transa, char transb, int m, int n, int k, double alpha, const double *A,
+                 int lda, const double *B, int ldb, double beta, double *C, int ldc, int slices,
+                 int exact, cudaStream_t stream);
+
+/*
  * purl_urv_truncate -- rank-k approximation of Section 5:
  *   A_k = U(:,1:k) R(1:k,:) V^T   (m x n, written to Ak, ldak >= m), 0 <= k <= n.
  * purl_urv_reconstruct is the k = n case (U R V^T).
@@ -142,6 +163,26 @@ int purl_urv_reconstruct(int m, int n, const double *U, int ldu, const double *R
  * `stream`.
  */
 int purl_device_status(cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Diagnostics (no counterpart in the paper; used by the benchmark).
+ * ------------------------------------------------------------------------ */
+
+/* Number of kernels this library has launched in this process. */
+unsigned long long purl_launch_count(void);
+
+/* Opt-in timing: while enabled, every kernel launch is bracketed by two CUDA
+ * events recorded on the stream it runs on, and its device time, algorithmic
+ * flops and algorithmic bytes are booked to its class:
+ *   0 gemm_f64 (FP64 DFMA products), 1 panel_qr (Householder panels),
+ *   2 gemm_tc (BF16 tensor-core products), 3 split (FP64 -> BF16 slicing),
+ *   4 other (RNG, T factors, reductions, copies, sign fixes).
+ * purl_profile_read synchronises the pending events of all classes and
+ * returns the totals since the last purl_profile_reset (-1 for a bad class). */
+void purl_profile_enable(int on);
+void purl_profile_reset(void);
+int purl_profile_read(int cls, long long *launches, double *ms, double *flops, double *bytes);
+const char *purl_profile_class_name(int cls);
 
 #ifdef __cplusplus
 }

@@ -39,9 +39,16 @@ SIGNATURES = {
     "purl_qr": (_i, [_i, _i, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
     "purl_qr_workspace_bytes": (_sz, [_i, _i, _i]),
     "purl_gemm_f64": (_i, [_c, _c, _i, _i, _i, _d, _p, _i, _p, _i, _d, _p, _i, _p]),
+    "purl_gemm_tc": (_i, [_c, _c, _i, _i, _i, _d, _p, _i, _p, _i, _d, _p, _i, _i, _i, _p]),
     "purl_urv_truncate": (_i, [_i, _i, _i, _p, _i, _p, _i, _p, _i, _p, _i, _p]),
     "purl_urv_reconstruct": (_i, [_i, _i, _p, _i, _p, _i, _p, _i, _p, _i, _p]),
     "purl_device_status": (_i, [_p]),
+    "purl_launch_count": (ctypes.c_ulonglong, []),
+    "purl_profile_enable": (None, [_i]),
+    "purl_profile_reset": (None, []),
+    "purl_profile_read": (_i, [_i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_d),
+                               ctypes.POINTER(_d), ctypes.POINTER(_d)]),
+    "purl_profile_class_name": (ctypes.c_char_p, [_i]),
 }
 
 _lock = threading.Lock()
@@ -189,6 +196,24 @@ def purl_gemm_f64(transa: str, transb: str, A, B, alpha: float = 1.0, beta: floa
     return C
 
 
+def purl_gemm_tc(transa: str, transb: str, A, B, alpha: float = 1.0, beta: float = 0.0, C=None,
+                 slices: int = 3, exact: bool = False, stream=None):
+    """C = alpha op(A) op(B) + beta C on the BF16 tensor cores with `slices` BF16 slices per operand."""
+    _cuda_check(A, B)
+    m = A.shape[0] if transa == "N" else A.shape[1]
+    k = A.shape[1] if transa == "N" else A.shape[0]
+    n = B.shape[1] if transb == "N" else B.shape[0]
+    if C is None:
+        C = empty_colmajor(m, n, A.device)
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs C")
+    _cuda_check(C)
+    st = lib().purl_gemm_tc(transa.encode(), transb.encode(), m, n, k, alpha, _ptr(A), _ld(A), _ptr(B),
+                            _ld(B), beta, _ptr(C), _ld(C), slices, int(bool(exact)), _stream(stream))
+    _check("purl_gemm_tc", st)
+    return C
+
+
 def purl_urv_truncate(U, R, V, k: int, out=None, stream=None):
     _cuda_check(U, R, V)
     m, n = U.shape
@@ -211,3 +236,29 @@ def purl_urv_reconstruct(U, R, V, out=None, stream=None):
 
 def purl_device_status(stream=None) -> int:
     return int(lib().purl_device_status(_stream(stream)))
+
+
+def purl_launch_count() -> int:
+    return int(lib().purl_launch_count())
+
+
+def purl_profile_enable(on: bool = True):
+    lib().purl_profile_enable(int(bool(on)))
+
+
+def purl_profile_reset():
+    lib().purl_profile_reset()
+
+
+PROFILE_CLASSES = ("gemm_f64", "panel_qr", "gemm_tc", "split", "other")
+
+
+def purl_profile_read() -> dict:
+    """{class name: {launches, ms, flops, bytes}} since the last reset (synchronises)."""
+    out = {}
+    for cls, name in enumerate(PROFILE_CLASSES):
+        n = ctypes.c_longlong(0)
+        ms, fl, by = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        lib().purl_profile_read(cls, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by))
+        out[name] = {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
+    return out

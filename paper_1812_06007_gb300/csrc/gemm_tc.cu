@@ -1,0 +1,349 @@
+// gemm_tc.cu -- BF16 tensor-core product engine for sm_103a: TMA loads into
+// 128-byte-swizzled shared memory, tcgen05.mma (kind::f16, BF16 x BF16 ->
+// FP32) issued by one thread, the accumulator in tensor memory (TMEM), and an
+// epilogue that reads TMEM with tcgen05.ld.
+//
+// This is the "efficient matrix-matrix multiplication routine" of Section 3
+// for the mixed-precision path: the power-step products (one BF16 slice per
+// operand) and, with 2 or 3 slices per operand, the compensated products of
+// A V, of every QR trailing update and of Q formation.
+//
+// CTA = 6 warps: warp 0 issues TMA loads, warp 1 allocates TMEM and issues the
+// MMAs, warps 2-5 run the epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
+// Tile 128 x BN x 64; a multi-stage shared-memory ring with full/empty
+// mbarriers; every wait is bounded and records PURL_ERR_TIMEOUT on expiry.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "profile.cuh"
+#include "tc.cuh"
+#include "tc_ptx.cuh"
+
+namespace purl {
+
+namespace {
+
+constexpr int TC_THREADS = 192;
+constexpr int TC_GROUP = 16;
+constexpr int kSmemBudget = 200 * 1024;
+
+template <int BN, int S>
+struct TcCfg {
+  static constexpr int A_BYTES = TC_BM * TC_BK * 2;
+  static constexpr int B_BYTES = BN * TC_BK * 2;
+  static constexpr int STAGE_BYTES = S * (A_BYTES + B_BYTES);
+  static constexpr int STAGES_RAW = kSmemBudget / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+  static_assert(STAGES >= 2, "tile too large for a 2-stage pipeline");
+  static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "BN");
+};
+
+template <int BN, int S>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   TcView va, TcView vb, int M, int N, int K, int k_chunk, TcEpilogue ep,
+                   DeviceControl *ctrl) {
+  using Cfg = TcCfg<BN, S>;
+  constexpr int STAGES = Cfg::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // grouped raster: consecutive blocks walk TC_GROUP M-tiles before moving to
+  // the next N-tile, so a wave shares A and B tiles in L2
+  const int tiles_m = (M + TC_BM - 1) / TC_BM, tiles_n = (N + BN - 1) / BN;
+  const int pid = blockIdx.x;
+  const int per_group = TC_GROUP * tiles_n;
+  const int first_m = (pid / per_group) * TC_GROUP;
+  const int gsize = min(tiles_m - first_m, TC_GROUP);
+  const int m0 = (first_m + (pid % per_group) % gsize) * TC_BM;
+  const int n0 = ((pid % per_group) / gsize) * BN;
+  const int kb0 = blockIdx.y * k_chunk;
+  const int kend = min(K, kb0 + k_chunk);
+  const int nkb = (kend - kb0 + TC_BK - 1) / TC_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&acc_bar, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"((uint32_t)Cfg::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int st = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(&empty_bar[st], ph ^ 1u, ctrl, &s_abort)) break;
+        mbar_arrive_expect_tx(&full_bar[st], (uint32_t)Cfg::STAGE_BYTES);
+        uint8_t *sa = smem + (size_t)st * Cfg::STAGE_BYTES;
+        uint8_t *sb = sa + S * Cfg::A_BYTES;
+        const int kx = kb0 + kb * TC_BK;
+#pragma unroll
+        for (int s = 0; s < S; ++s) tma_load_3d(sa + s * Cfg::A_BYTES, &tmA, &full_bar[st], va.r0 + kx, va.c0 + m0, s);
+#pragma unroll
+        for (int s = 0; s < S; ++s) tma_load_3d(sb + s * Cfg::B_BYTES, &tmB, &full_bar[st], vb.r0 + kx, vb.c0 + n0, s);
+        issued = kb + 1;
+      }
+      // never leave the block with copies in flight: the last use of every stage
+      // must have landed (bounded; normally already true)
+      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+        mbar_wait(&full_bar[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, ctrl, &s_abort, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int st = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(&full_bar[st], ph, ctrl, &s_abort)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
+        const uint32_t sb = sa + S * Cfg::A_BYTES;
+        int prod = 0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+#pragma unroll
+          for (int t = 0; t < S - s; ++t) {
+#pragma unroll
+            for (int k = 0; k < TC_BK / 16; ++k) {
+              const uint64_t ad = sw128_desc(sa + s * Cfg::A_BYTES + k * 32);
+              const uint64_t bd = sw128_desc(sb + t * Cfg::B_BYTES + k * 32);
+              tc_mma(tmem, ad, bd, idesc, (kb > 0 || prod > 0 || k > 0) ? 1u : 0u);
+            }
+            ++prod;
+          }
+        }
+        tc_commit(&empty_bar[st]);
+      }
+      tc_commit(&acc_bar);
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const bool ok = mbar_wait(&acc_bar, 0, ctrl, &s_abort);
+    tc_fence_after();
+    if (ok && nkb > 0) {
+      const int lane_base = 32 * (warp & 3);
+      const int row = m0 + lane_base + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)c0, v);
+        if (row < M) {
+          if (ep.mode == 0) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int col = n0 + c0 + j;
+              if (col < N) {
+                const double acc = (double)__uint_as_float(v[j]);
+                double *p = ep.C + row + (long long)col * ep.ldc;
+                const double x = (ep.beta == 0.0) ? ep.alpha * acc : fma(ep.alpha, acc, ep.beta * *p);
+                *p = x;
+                if (ep.out.base)
+                  write_slices(x, ep.out.base + row + (long long)col * ep.out.ld, ep.out.plane, ep.out.S);
+              }
+            }
+          } else {
+            float *P = ep.P + (long long)blockIdx.y * M * N;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int col = n0 + c0 + j;
+              if (col < N) P[row + (long long)col * M] = __uint_as_float(v[j]);
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    // every MMA of this block must be complete before TMEM is released
+    if (lane == 0) mbar_wait(&acc_bar, 0, ctrl, &s_abort, false);
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)Cfg::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------- slicing ----
+__global__ void split_kernel(int R, int Cc, const double *__restrict__ X, long long ldx, Slices dst) {
+  long long total = (long long)R * Cc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(e % R), c = (int)(e / R);
+    write_slices(X[r + c * ldx], dst.base + r + c * dst.ld, dst.plane, dst.S);
+  }
+}
+
+// dst (Cc x R) = slices of X^T; 32 x 32 tiles through shared memory.
+__global__ void split_t_kernel(int R, int Cc, const double *__restrict__ X, long long ldx, Slices dst) {
+  __shared__ double tile[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    int r = r0 + threadIdx.x, c = c0 + j;
+    tile[j][threadIdx.x] = (r < R && c < Cc) ? X[r + (long long)c * ldx] : 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    int c = c0 + threadIdx.x, r = r0 + j;  // dst(c, r) = X(r, c)
+    if (r < R && c < Cc) write_slices(tile[threadIdx.x][j], dst.base + c + (long long)r * dst.ld, dst.plane, dst.S);
+  }
+}
+
+template <int BN, int S>
+int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcView va, TcView vb, int M, int N, int K,
+              int k_chunk, int splits, const TcEpilogue &ep, DeviceControl *ctrl, cudaStream_t s) {
+  using Cfg = TcCfg<BN, S>;
+  static thread_local int attr_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
+    if (cudaFuncSetAttribute(tc_gemm_kernel<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) !=
+        cudaSuccess)
+      return PURL_ERR_CUDA;
+    attr_dev = dev;
+  }
+  long long tiles = (long long)ceil_div(M, TC_BM) * ceil_div(N, BN);
+  if (tiles > 0x7fffffffLL || splits > 65535) return PURL_ERR_UNSUPPORTED;
+  dim3 grid((unsigned)tiles, splits);
+  int prods = S * (S + 1) / 2;
+  double flops = 2.0 * M * (double)N * K;  // algorithmic: one product, not one per slice pair
+  double bytes = (double)S * 2.0 * ((double)M * K + (double)N * K) +
+                 (ep.mode == 0 ? 8.0 * M * N * (ep.beta != 0.0 ? 2 : 1) + (ep.out.base ? 2.0 * ep.out.S * M * N : 0)
+                               : 4.0 * M * N * splits);
+  (void)prods;
+  LaunchScope ls(KC_GEMM_TC, s, flops, bytes);
+  tc_gemm_kernel<BN, S><<<grid, TC_THREADS, Cfg::SMEM, s>>>(ma, mb, va, vb, M, N, K, k_chunk, ep, ctrl);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side ---
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map over the slices of an operand: x = row (K, contiguous) limited to
+// k_end, y = column (M or N) limited to c_end, z = slice.
+int make_map(CUtensorMap *map, const Slices &X, int k_end, int c_end, int box_rows) {
+  auto enc = encode_fn();
+  if (!enc) return PURL_ERR_UNSUPPORTED;
+  if (((uintptr_t)X.base & 15) != 0 || (X.ld % 8) != 0 || (X.plane % 8) != 0) return PURL_ERR_UNSUPPORTED;
+  cuuint64_t dims[3] = {(cuuint64_t)k_end, (cuuint64_t)c_end, (cuuint64_t)X.S};
+  cuuint64_t strides[2] = {(cuuint64_t)X.ld * 2, (cuuint64_t)X.plane * 2};
+  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, X.base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? PURL_OK : PURL_ERR_UNSUPPORTED;
+}
+
+
+int split_slices(int R, int Cc, const double *X, long long ldx, Slices dst, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  long long total = (long long)R * Cc;
+  if (total == 0) return PURL_OK;
+  long long g = (total + 255) / 256;
+  if (g > (long long)di->num_sms * 16) g = (long long)di->num_sms * 16;
+  LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * dst.S) * total);
+  split_kernel<<<(int)g, 256, 0, s>>>(R, Cc, X, ldx, dst);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+int split_slices_t(int R, int Cc, const double *X, long long ldx, Slices dst, cudaStream_t s) {
+  if ((long long)R * Cc == 0) return PURL_OK;
+  dim3 grid(ceil_div(R, 32), ceil_div(Cc, 32));
+  if (grid.y > 65535) return PURL_ERR_UNSUPPORTED;
+  LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc);
+  split_t_kernel<<<grid, dim3(32, 8), 0, s>>>(R, Cc, X, ldx, dst);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+void tc_choose_splits(int M, int N, int K, int num_sms, int max_splits, int *splits, int *k_chunk) {
+  long long tiles = (long long)ceil_div(M, TC_BM) * ceil_div(N, 128);
+  long long want = (2LL * num_sms + tiles - 1) / tiles;
+  long long maxs = (K + 255) / 256;
+  long long sp = want < maxs ? want : maxs;
+  if (sp < 1) sp = 1;
+  if (sp > max_splits) sp = max_splits;
+  int chunk = ceil_div(ceil_div(K, (int)sp), TC_BK) * TC_BK;
+  *k_chunk = chunk > 0 ? chunk : TC_BK;
+  *splits = K > 0 ? ceil_div(K, *k_chunk) : 1;
+}
+
+// Views: A rows [a_r0, a_r0+K) x cols [a_c0, a_c0+M); same for B with N.
+int tc_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0, int b_c0, int M, int N, int K,
+                 int S, const TcEpilogue &ep, int splits, int k_chunk, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  if (M <= 0 || N <= 0) return PURL_OK;
+  if (K <= 0 || k_chunk <= 0 || (k_chunk % TC_BK) != 0 || splits != ceil_div(K, k_chunk)) return PURL_ERR_UNSUPPORTED;
+  if (S < 1 || S > 3 || A.S < S || B.S < S) return PURL_ERR_UNSUPPORTED;
+  if ((a_r0 % 8) != 0 || (b_r0 % 8) != 0) return PURL_ERR_UNSUPPORTED;
+  if (ep.mode == 1 && !ep.P) return PURL_ERR_UNSUPPORTED;
+  if (ep.mode == 0 && !ep.C) return PURL_ERR_UNSUPPORTED;
+  // N tile: the widest that fits the smem budget for S slices
+  int BN = N > 128 ? 256 : (N > 64 ? 128 : (N > 32 ? 64 : 32));
+  if (S == 3 && BN > 128) BN = 128;
+  if (S == 2 && BN > 256) BN = 256;
+  CUtensorMap ma, mb;
+  PURL_TRY(make_map(&ma, A, a_r0 + K, a_c0 + M, TC_BM));
+  PURL_TRY(make_map(&mb, B, b_r0 + K, b_c0 + N, BN));
+  TcView va{a_r0, a_c0}, vb{b_r0, b_c0};
+#define PURL_TC_CASE(BN_, S_) \
+  if (BN == BN_ && S == S_) return launch_tc<BN_, S_>(ma, mb, va, vb, M, N, K, k_chunk, splits, ep, di->ctrl, s);
+  PURL_TC_CASE(32, 1) PURL_TC_CASE(64, 1) PURL_TC_CASE(128, 1) PURL_TC_CASE(256, 1)
+  PURL_TC_CASE(32, 2) PURL_TC_CASE(64, 2) PURL_TC_CASE(128, 2) PURL_TC_CASE(256, 2)
+  PURL_TC_CASE(32, 3) PURL_TC_CASE(64, 3) PURL_TC_CASE(128, 3)
+#undef PURL_TC_CASE
+  return PURL_ERR_UNSUPPORTED;
+}
+
+int tc_gemm(const Slices &A, const Slices &B, int M, int N, int K, int S, const TcEpilogue &ep, int splits,
+            int k_chunk, cudaStream_t s) {
+  return tc_gemm_view(A, 0, 0, B, 0, 0, M, N, K, S, ep, splits, k_chunk, s);
+}
+
+}  // namespace purl

@@ -1,0 +1,369 @@
+// gemm_tcx.cu -- BF16 tensor-core products with EXACT accumulation (sm_103a).
+//
+// The FP32 accumulator of tcgen05.mma does not round to nearest: measured on
+// this GPU, a compensated 3-slice product over K = 512 is no more accurate
+// than a 2-slice one (error ~ (K/16) 2^-23 of |C|).  This kernel removes that
+// floor with the splitting of Ozaki et al. (error-free transformation of a
+// matrix product into exact low-precision products): every operand row is
+// scaled by a power of two and cut into slices of small integers
+// (|alpha| <= 128, exact in BF16), so every product is an integer below 2^14
+// and every partial sum of one slice-pair class over 256 of K is an integer
+// below 2^24 -- exactly representable, so the accumulator never rounds.
+//
+// Per 256 of K ("chunk") the classes d = s + t (S of them) accumulate in
+// their own TMEM columns; two chunk buffers alternate so the MMA warp fills
+// one while the epilogue warps drain the other into per-thread double-FP32
+// (hi, lo) sums by the error-free two-sum.  The only error left is the
+// slicing itself: 2^(-8S) of each operand row's scale.
+//
+// Used by the mixed-precision QR (V^T C, the trailing update C - V W, the
+// Gram matrix V^T V, Q formation) and by A V (Section 3, Eq. (6)).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "profile.cuh"
+#include "tc.cuh"
+#include "tc_ptx.cuh"
+
+namespace purl {
+
+namespace {
+
+constexpr int TCX_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int TCX_BN = 64;
+constexpr int TCX_KBC = 4;        // k-blocks per exact chunk (4 x 64 = 256 of K)
+constexpr int TCX_GROUP = 16;
+
+template <int S>
+struct TcxCfg {
+  static constexpr int A_BYTES = TC_BM * TC_BK * 2;
+  static constexpr int B_BYTES = TCX_BN * TC_BK * 2;
+  static constexpr int STAGE_BYTES = S * (A_BYTES + B_BYTES);
+  static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  static constexpr int USED_COLS = 2 * S * TCX_BN;
+  static constexpr int TMEM_COLS = USED_COLS <= 128 ? 128 : (USED_COLS <= 256 ? 256 : 512);
+  static_assert(STAGES >= 2, "stages");
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// (hi, lo) += x, hi + lo exact up to the rounding of lo (error-free two-sum).
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+// x = 2^e * sum_s alpha_s 2^(-7-8s), alpha_s = integers in [-128, 128].
+__device__ __forceinline__ void write_exact_slices(double x, int e, __nv_bfloat16 *dst, long long plane, int S) {
+  double t = ldexp(x, -e) * 128.0;
+  for (int s = 0; s < S; ++s) {
+    const double a = rint(t);
+    dst[s * plane] = __double2bfloat16(a);  // exact: |a| <= 128 (<= 129 with rounding slack)
+    t = (t - a) * 256.0;
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(TCX_THREADS, 1)
+    tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcView va,
+                    TcView vb, int M, int N, int K, int k_chunk, const int *__restrict__ scA,
+                    const int *__restrict__ scB, TcEpilogue ep, DeviceControl *ctrl) {
+  using Cfg = TcxCfg<S>;
+  constexpr int STAGES = Cfg::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t tfull_bar[2];
+  __shared__ __align__(8) uint64_t tempty_bar[2];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_m = (M + TC_BM - 1) / TC_BM, tiles_n = (N + TCX_BN - 1) / TCX_BN;
+  const int pid = blockIdx.x;
+  const int per_group = TCX_GROUP * tiles_n;
+  const int first_m = (pid / per_group) * TCX_GROUP;
+  const int gsize = min(tiles_m - first_m, TCX_GROUP);
+  const int m0 = (first_m + (pid % per_group) % gsize) * TC_BM;
+  const int n0 = ((pid % per_group) / gsize) * TCX_BN;
+  const int kb0 = blockIdx.y * k_chunk;
+  const int kend = min(K, kb0 + k_chunk);
+  const int nkb = (kend - kb0 + TC_BK - 1) / TC_BK;
+  const int nch = (nkb + TCX_KBC - 1) / TCX_KBC;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], 4);
+    }
+    mbar_init(&done_bar, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"((uint32_t)Cfg::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int st = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(&empty_bar[st], ph ^ 1u, ctrl, &s_abort)) break;
+        mbar_arrive_expect_tx(&full_bar[st], (uint32_t)Cfg::STAGE_BYTES);
+        uint8_t *sa = smem + (size_t)st * Cfg::STAGE_BYTES;
+        uint8_t *sb = sa + S * Cfg::A_BYTES;
+        const int kx = kb0 + kb * TC_BK;
+#pragma unroll
+        for (int s = 0; s < S; ++s) tma_load_3d(sa + s * Cfg::A_BYTES, &tmA, &full_bar[st], va.r0 + kx, va.c0 + m0, s);
+#pragma unroll
+        for (int s = 0; s < S; ++s) tma_load_3d(sb + s * Cfg::B_BYTES, &tmB, &full_bar[st], vb.r0 + kx, vb.c0 + n0, s);
+        issued = kb + 1;
+      }
+      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+        mbar_wait(&full_bar[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, ctrl, &s_abort, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(TC_BM, TCX_BN);
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int c = kb / TCX_KBC, b = c & 1, kin = kb % TCX_KBC;
+        if (kin == 0) {
+          if (!mbar_wait(&tempty_bar[b], ((uint32_t)(c >> 1) & 1u) ^ 1u, ctrl, &s_abort)) break;
+          tc_fence_after();
+        }
+        const int st = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(&full_bar[st], ph, ctrl, &s_abort)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
+        const uint32_t sb = sa + S * Cfg::A_BYTES;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+#pragma unroll
+          for (int t = 0; t < S - s; ++t) {
+            const uint32_t dcol = tmem + (uint32_t)((b * S + s + t) * TCX_BN);
+#pragma unroll
+            for (int k = 0; k < TC_BK / 16; ++k) {
+              const uint64_t ad = sw128_desc(sa + s * Cfg::A_BYTES + k * 32);
+              const uint64_t bd = sw128_desc(sb + t * Cfg::B_BYTES + k * 32);
+              // the first product of class s+t in a chunk overwrites its accumulator
+              tc_mma(dcol, ad, bd, idesc, (kin == 0 && s == 0 && k == 0) ? 0u : 1u);
+            }
+          }
+        }
+        tc_commit(&empty_bar[st]);
+        if (kin == TCX_KBC - 1 || kb == nkb - 1) tc_commit(&tfull_bar[b]);
+      }
+      tc_commit(&done_bar);
+    }
+  } else {
+    // ---------------- epilogue: drain chunks into double-FP32 sums ----------------
+    const int lane_base = 32 * (warp & 3);
+    float hi[TCX_BN], lo[TCX_BN];
+#pragma unroll
+    for (int j = 0; j < TCX_BN; ++j) hi[j] = lo[j] = 0.0f;
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+      const int b = c & 1;
+      if (!mbar_wait(&tfull_bar[b], (uint32_t)(c >> 1) & 1u, ctrl, &s_abort)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int d = 0; d < S; ++d) {
+        const float w = d == 0 ? 1.0f : (d == 1 ? 0x1.0p-8f : 0x1.0p-16f);
+#pragma unroll
+        for (int h = 0; h < TCX_BN / 32; ++h) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)((b * S + d) * TCX_BN + h * 32), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) two_sum_acc(hi[h * 32 + j], lo[h * 32 + j], __uint_as_float(v[j]) * w);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty_bar[b]);
+    }
+    const int row = m0 + lane_base + lane;
+    if (ok && nkb > 0 && row < M) {
+      const int ea = scA[va.c0 + row];
+#pragma unroll
+      for (int j = 0; j < TCX_BN; ++j) {
+        const int col = n0 + j;
+        if (col < N) {
+          const double val = ldexp((double)hi[j] + (double)lo[j], ea + scB[vb.c0 + col] - 14);
+          if (ep.mode == 0) {
+            double *p = ep.C + row + (long long)col * ep.ldc;
+            const double x = (ep.beta == 0.0) ? ep.alpha * val : fma(ep.alpha, val, ep.beta * *p);
+            *p = x;
+            if (ep.out.base) {
+              __nv_bfloat16 *o = ep.out.base + row + (long long)col * ep.out.ld;
+              if (ep.out.scale) write_exact_slices(x, ep.out.scale[col], o, ep.out.plane, ep.out.S);
+              else write_slices(x, o, ep.out.plane, ep.out.S);
+            }
+          } else {
+            ep.Pd[(long long)blockIdx.y * M * N + row + (long long)col * M] = val;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    if (lane == 0) mbar_wait(&done_bar, 0, ctrl, &s_abort, false);
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// One block per column: exponent of the column maximum (or the given one),
+// then the exact slices of the column.
+__global__ void __launch_bounds__(256) split_exact_kernel(int R, int Cc, const double *__restrict__ X, long long ldx,
+                                                          Slices dst, const int *__restrict__ scale_from) {
+  __shared__ double red[8];
+  __shared__ int s_e;
+  for (int c = blockIdx.x; c < Cc; c += gridDim.x) {
+    const double *col = X + (long long)c * ldx;
+    if (scale_from) {
+      if (threadIdx.x == 0) s_e = scale_from[c];
+    } else {
+      double mx = 0.0;
+      for (int r = threadIdx.x; r < R; r += 256) mx = fmax(mx, fabs(col[r]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < 8; ++w) m = fmax(m, red[w]);
+        int e = 0;
+        if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |x| < 2^e
+        s_e = e;
+      }
+    }
+    __syncthreads();
+    const int e = s_e;
+    if (threadIdx.x == 0 && dst.scale) dst.scale[c] = e;
+    for (int r = threadIdx.x; r < R; r += 256) write_exact_slices(col[r], e, dst.base + r + (long long)c * dst.ld, dst.plane, dst.S);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) col_norm_exp_kernel(int R, int Cc, const double *__restrict__ X, long long ldx,
+                                                           int *e_out) {
+  __shared__ double red[8];
+  for (int c = blockIdx.x; c < Cc; c += gridDim.x) {
+    const double *col = X + (long long)c * ldx;
+    double s = 0.0;
+    for (int r = threadIdx.x; r < R; r += 256) s = fma(col[r], col[r], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      int e = 0;
+      if (t > 0.0) frexp(sqrt(t) * (1.0 + 0x1.0p-20), &e);
+      e_out[c] = e;
+    }
+    __syncthreads();
+  }
+}
+
+template <int S>
+int launch_tcx(const CUtensorMap &ma, const CUtensorMap &mb, TcView va, TcView vb, int M, int N, int K, int k_chunk,
+               int splits, const int *scA, const int *scB, const TcEpilogue &ep, DeviceControl *ctrl,
+               cudaStream_t s) {
+  using Cfg = TcxCfg<S>;
+  static thread_local int attr_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
+    if (cudaFuncSetAttribute(tcx_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) !=
+        cudaSuccess)
+      return PURL_ERR_CUDA;
+    attr_dev = dev;
+  }
+  long long tiles = (long long)ceil_div(M, TC_BM) * ceil_div(N, TCX_BN);
+  if (tiles > 0x7fffffffLL || splits > 65535) return PURL_ERR_UNSUPPORTED;
+  double flops = 2.0 * M * (double)N * K;
+  double bytes = (double)S * 2.0 * ((double)M * K + (double)N * K) +
+                 (ep.mode == 0 ? 8.0 * M * N * (ep.beta != 0.0 ? 2 : 1) + (ep.out.base ? 2.0 * ep.out.S * M * N : 0)
+                               : 8.0 * M * N * splits);
+  LaunchScope ls(KC_GEMM_TC, s, flops, bytes);
+  tcx_gemm_kernel<S><<<dim3((unsigned)tiles, splits), TCX_THREADS, Cfg::SMEM, s>>>(ma, mb, va, vb, M, N, K, k_chunk,
+                                                                                  scA, scB, ep, ctrl);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+}  // namespace
+
+int split_exact(int R, int Cc, const double *X, long long ldx, Slices dst, const int *scale_from, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  if (Cc <= 0) return PURL_OK;
+  if (!scale_from && !dst.scale) return PURL_ERR_UNSUPPORTED;
+  int grid = Cc < di->num_sms * 32 ? Cc : di->num_sms * 32;
+  LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc);
+  split_exact_kernel<<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+int column_norm_exponents(int R, int Cc, const double *X, long long ldx, int *e, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  if (Cc <= 0) return PURL_OK;
+  int grid = Cc < di->num_sms * 32 ? Cc : di->num_sms * 32;
+  LaunchScope ls(KC_OTHER, s, 0.0, 8.0 * (double)R * Cc);
+  col_norm_exp_kernel<<<grid, 256, 0, s>>>(R, Cc, X, ldx, e);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+int tcx_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0, int b_c0, int M, int N, int K, int S,
+                  const TcEpilogue &ep, int splits, int k_chunk, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  if (M <= 0 || N <= 0) return PURL_OK;
+  if (K <= 0 || k_chunk <= 0 || (k_chunk % (TC_BK * TCX_KBC)) != 0 || splits != ceil_div(K, k_chunk))
+    return PURL_ERR_UNSUPPORTED;
+  if (S < 1 || S > 3 || A.S < S || B.S < S || !A.scale || !B.scale) return PURL_ERR_UNSUPPORTED;
+  if ((a_r0 % 8) != 0 || (b_r0 % 8) != 0) return PURL_ERR_UNSUPPORTED;
+  if (ep.mode == 2 && !ep.Pd) return PURL_ERR_UNSUPPORTED;
+  if (ep.mode == 0 && !ep.C) return PURL_ERR_UNSUPPORTED;
+  if (ep.mode != 0 && ep.mode != 2) return PURL_ERR_UNSUPPORTED;
+  CUtensorMap ma, mb;
+  PURL_TRY(make_map(&ma, A, a_r0 + K, a_c0 + M, TC_BM));
+  PURL_TRY(make_map(&mb, B, b_r0 + K, b_c0 + N, TCX_BN));
+  TcView va{a_r0, a_c0}, vb{b_r0, b_c0};
+  if (S == 1) return launch_tcx<1>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
+  if (S == 2) return launch_tcx<2>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
+  return launch_tcx<3>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
+}
+
+}  // namespace purl

@@ -23,6 +23,7 @@
 // the factorization unique).
 #include "common.cuh"
 #include "qr.cuh"
+#include "profile.cuh"
 
 namespace purl {
 
@@ -246,6 +247,22 @@ __global__ void copy_kernel(int m, int n, const double *X, long long ldx, double
   }
 }
 
+// Y (Cc x R) = X^T (X is R x Cc), 32 x 32 tiles through shared memory.
+__global__ void transpose_kernel(int R, int Cc, const double *__restrict__ X, long long ldx, double *Y,
+                                 long long ldy) {
+  __shared__ double tile[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    int r = r0 + threadIdx.x, c = c0 + j;
+    tile[j][threadIdx.x] = (r < R && c < Cc) ? X[r + (long long)c * ldx] : 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    int c = c0 + threadIdx.x, r = r0 + j;
+    if (r < R && c < Cc) Y[c + (long long)r * ldy] = tile[threadIdx.x][j];
+  }
+}
+
 int grid_for(long long total, const DeviceInfo *di) {
   long long g = (total + 255) / 256;
   long long cap = (long long)di->num_sms * 16;
@@ -307,7 +324,8 @@ static int apply_block(int rows, int bw, int nc, double *C, int ldc, const doubl
   int splits, chunk;
   choose_splits(bw, nc, rows, di->num_sms, &splits, &chunk);
   PURL_TRY(gemm_f64_splitk(true, false, bw, nc, rows, splits, chunk, w.Vb, rows, C, ldc, w.Wp, s));
-  reduce_tmul_kernel<<<ceil_div(nc, 32), 256, 0, s>>>(bw, nc, splits, w.Wp, T, trans, w.W2);
+  { LaunchScope ls(KC_OTHER, s);
+  reduce_tmul_kernel<<<ceil_div(nc, 32), 256, 0, s>>>(bw, nc, splits, w.Wp, T, trans, w.W2); }
   PURL_CUDA_TRY(cudaGetLastError());
   return gemm_f64(false, false, rows, nc, bw, -1.0, w.Vb, rows, w.W2, bw, 1.0, C, ldc, s);
 }
@@ -335,15 +353,18 @@ int qr_factor_f64(int m, int n, double *F, int ldf, QrWork &w, cudaStream_t s) {
     long long ldf_ll = ldf, ldv_ll = ldv;
     void *args[] = {&rows, &bw, &ch, &Fp, &ldf_ll, &w.Vb, &ldv_ll, &taup, &w.part, &w.rowk, &cnt,
                     (void *)&di->ctrl};
-    PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel, dim3(P), dim3(PNT), args,
-                                              smem, s));
+    {
+      LaunchScope ls(KC_PANEL, s, 2.0 * rows * bw * (double)bw, 16.0 * rows * bw);
+      PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel, dim3(P), dim3(PNT),
+                                                args, smem, s));
+    }
     // T factor from the Gram matrix V^T V
     int gs, gchunk;
     choose_splits(bw, bw, rows, di->num_sms, &gs, &gchunk);
     if (gs > QR_MAX_SPLITS) gs = QR_MAX_SPLITS, gchunk = ceil_div(ceil_div(rows, gs), 16) * 16;
     PURL_TRY(gemm_f64_splitk(true, false, bw, bw, rows, gs, gchunk, w.Vb, ldv, w.Vb, ldv, w.Gp, s));
     double *Tp = w.T + (size_t)p * QR_B * QR_B;
-    larft_kernel<<<1, 256, 0, s>>>(bw, gs, w.Gp, taup, Tp);
+    { LaunchScope ls(KC_OTHER, s); larft_kernel<<<1, 256, 0, s>>>(bw, gs, w.Gp, taup, Tp); }
     PURL_CUDA_TRY(cudaGetLastError());
     // trailing update with Q_p^T
     PURL_TRY(apply_block(rows, bw, n - j0 - bw, Fp + (size_t)bw * ldf, ldf, Tp, true, w, di, s));
@@ -356,15 +377,16 @@ int qr_form_q_f64(int m, int n, const double *F, int ldf, QrWork &w, double *Q, 
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
   if (m == 0 || n == 0) return PURL_OK;
-  set_identity_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, Q, ldq);
+  { LaunchScope ls(KC_OTHER, s); set_identity_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, Q, ldq); }
   PURL_CUDA_TRY(cudaGetLastError());
   int npan = ceil_div(n, QR_B);
   for (int p = npan - 1; p >= 0; --p) {
     int j0 = p * QR_B;
     int bw = min(QR_B, n - j0);
     int rows = m - j0;
-    extract_v_kernel<<<grid_for((long long)rows * bw, di), 256, 0, s>>>(
-        rows, bw, F + j0 + (size_t)j0 * ldf, ldf, w.Vb, rows);
+    { LaunchScope ls(KC_OTHER, s);
+      extract_v_kernel<<<grid_for((long long)rows * bw, di), 256, 0, s>>>(
+          rows, bw, F + j0 + (size_t)j0 * ldf, ldf, w.Vb, rows); }
     PURL_CUDA_TRY(cudaGetLastError());
     const double *Tp = w.T + (size_t)p * QR_B * QR_B;
     PURL_TRY(apply_block(rows, bw, n - j0, Q + j0 + (size_t)j0 * ldq, ldq, Tp, false, w, di, s));
@@ -378,7 +400,7 @@ int qr_sign_fix(int m, int n, const double *F, int ldf, double *Q, int ldq, doub
   if (!di) return PURL_ERR_CUDA;
   long long tot = (Q ? (long long)m * n : 0) + (R ? (long long)n * n : 0);
   if (tot == 0) return PURL_OK;
-  sign_fix_kernel<<<grid_for(tot, di), 256, 0, s>>>(m, n, F, ldf, Q, ldq, R, ldr);
+  { LaunchScope ls(KC_OTHER, s); sign_fix_kernel<<<grid_for(tot, di), 256, 0, s>>>(m, n, F, ldf, Q, ldq, R, ldr); }
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
@@ -386,7 +408,16 @@ int copy_matrix(int m, int n, const double *X, int ldx, double *Y, int ldy, cuda
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
   if ((long long)m * n == 0) return PURL_OK;
-  copy_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, X, ldx, Y, ldy);
+  { LaunchScope ls(KC_OTHER, s); copy_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, X, ldx, Y, ldy); }
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+int transpose_f64(int R, int Cc, const double *X, int ldx, double *Y, int ldy, cudaStream_t s) {
+  if ((long long)R * Cc == 0) return PURL_OK;
+  dim3 grid(ceil_div(R, 32), ceil_div(Cc, 32));
+  if (grid.y > 65535) return PURL_ERR_UNSUPPORTED;
+  { LaunchScope ls(KC_OTHER, s, 0.0, 16.0 * (double)R * Cc);
+    transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(R, Cc, X, ldx, Y, ldy); }
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 

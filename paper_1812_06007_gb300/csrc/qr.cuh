@@ -28,6 +28,7 @@ int qr_sign_fix(int m, int n, const double *F, int ldf, double *Q, int ldq, doub
                 cudaStream_t s);
 int qr_explicit(int m, int n, double *F, int ldf, double *Q, int ldq, double *R, int ldr,
                 int mode, QrWork &w, cudaStream_t s);
+int transpose_f64(int R, int Cc, const double *X, int ldx, double *Y, int ldy, cudaStream_t s);
 int copy_matrix(int m, int n, const double *X, int ldx, double *Y, int ldy, cudaStream_t s);
 
 }  // namespace purl

@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "qr.cuh"
+#include "tc.cuh"
 
 namespace purl {
 
@@ -250,6 +251,69 @@ int purl_gemm_f64(char transa, char transb, int m, int n, int k, double alpha, c
   if (ldc < (m > 1 ? m : 1)) return -13;
   if (!device_info()) return PURL_ERR_CUDA;
   return gemm_f64(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+}
+
+int purl_gemm_tc(char transa, char transb, int m, int n, int k, double alpha, const double *A,
+                 int lda, const double *B, int ldb, double beta, double *C, int ldc, int slices,
+                 int exact, cudaStream_t stream) {
+  bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
+  if (!ta && transa != 'N' && transa != 'n') return -1;
+  if (!tb && transb != 'N' && transb != 'n') return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  int arows = ta ? k : m, brows = tb ? n : k;
+  if (!A && (long long)m * k > 0) return -7;
+  if (lda < (arows > 1 ? arows : 1)) return -8;
+  if (!B && (long long)k * n > 0) return -9;
+  if (ldb < (brows > 1 ? brows : 1)) return -10;
+  if (!C && (long long)m * n > 0) return -12;
+  if (ldc < (m > 1 ? m : 1)) return -13;
+  if (slices < 1 || slices > 3) return -14;
+  if ((long long)m * n == 0) return PURL_OK;
+  if (!device_info()) return PURL_ERR_CUDA;
+  if (k == 0) return gemm_f64(false, false, m, n, 0, 0.0, A, lda, B, ldb, beta, C, ldc, stream);
+  size_t ea = slice_elems(k, m, slices), eb = slice_elems(k, n, slices);
+  size_t tmp = exact ? (size_t)k * (size_t)(m > n ? m : n) : 0;  // FP64 transpose staging
+  size_t bytes = sizeof(__nv_bfloat16) * (ea + eb) + sizeof(double) * tmp + sizeof(int) * ((size_t)m + n) + 2048;
+  Scratch scratch;
+  PURL_TRY(scratch.acquire(nullptr, 0, bytes, stream));
+  Arena ar;
+  ar.base = static_cast<char *>(scratch.ptr);
+  ar.size = bytes;
+  Slices sa = make_slices(ar.take<__nv_bfloat16>(ea), k, m, slices);
+  Slices sb = make_slices(ar.take<__nv_bfloat16>(eb), k, n, slices);
+  TcEpilogue ep;
+  ep.mode = 0;
+  ep.alpha = alpha;
+  ep.beta = beta;
+  ep.C = C;
+  ep.ldc = ldc;
+  if (!exact) {
+    // operand A: rows K, cols M (K-major); operand B: rows K, cols N
+    if (ta) PURL_TRY(split_slices(k, m, A, lda, sa, stream));
+    else PURL_TRY(split_slices_t(m, k, A, lda, sa, stream));
+    if (tb) PURL_TRY(split_slices_t(n, k, B, ldb, sb, stream));
+    else PURL_TRY(split_slices(k, n, B, ldb, sb, stream));
+    return tc_gemm(sa, sb, m, n, k, slices, ep, 1, ceil_div(k, 64) * 64, stream);
+  }
+  double *T = tmp ? ar.take<double>(tmp) : nullptr;
+  sa.scale = ar.take<int>(m);
+  sb.scale = ar.take<int>(n);
+  if (!ar.ok) return PURL_ERR_NOMEM;
+  if (ta) {
+    PURL_TRY(split_exact(k, m, A, lda, sa, nullptr, stream));
+  } else {
+    PURL_TRY(transpose_f64(m, k, A, lda, T, k, stream));
+    PURL_TRY(split_exact(k, m, T, k, sa, nullptr, stream));
+  }
+  if (tb) {
+    PURL_TRY(transpose_f64(n, k, B, ldb, T, k, stream));
+    PURL_TRY(split_exact(k, n, T, k, sb, nullptr, stream));
+  } else {
+    PURL_TRY(split_exact(k, n, B, ldb, sb, nullptr, stream));
+  }
+  return tcx_gemm_view(sa, 0, 0, sb, 0, 0, m, n, k, slices, ep, 1, ceil_div(k, 256) * 256, stream);
 }
 
 int purl_urv_truncate(int m, int n, int k, const double *U, int ldu, const double *R, int ldr,

@@ -8,8 +8,9 @@ Test matrices follow the recipe of Section 5: A = Uh diag(sigma) Vh^T with
 Uh, Vh Haar-distributed orthogonal factors.  A Haar factor is the Q of a QR
 of a seeded N(0,1) matrix with the signs fixed so that diag(R) > 0 (the
 footnote of Section 2.2 explains why the sign fix is needed for Haar).  The
-QR here is numpy's LAPACK (host) or torch's (device) -- a library routine
-used for input synthesis, never the code under test.
+QR here is numpy's LAPACK on the host -- a library routine used for input
+synthesis, never the code under test.  Inputs too large for a host QR use
+MixedOrthogonal factors (see below).
 
 sigma profiles:
   exponential  sigma_j = 10^(-d (j-1)/(n-1))     (decay to 10^-d)
@@ -61,38 +62,59 @@ def gaussian_matrix_np(m: int, n: int, seed: int) -> np.ndarray:
     return np.asfortranarray(np.random.default_rng(seed).standard_normal((m, n)))
 
 
-def _haar_torch(rows: int, cols: int, seed: int, device, dtype):
-    import torch
-    gen = torch.Generator(device=device)
-    gen.manual_seed(seed)
-    X = torch.randn(rows, cols, generator=gen, device=device, dtype=dtype)
-    Q, R = torch.linalg.qr(X)
-    d = torch.sign(torch.diagonal(R))
-    d[d == 0] = 1.0
-    return Q * d
+class MixedOrthogonal:
+    """Dense orthogonal N x N operator M = B1 P B2 for inputs too large for a
+    host QR: B1, B2 block-diagonal with Haar blocks (host numpy QR of seeded
+    Gaussian blocks, sign-fixed), P a seeded row permutation.  Every row of M
+    mixes every block, M is orthogonal to rounding, and it is applied in
+    O(N^2 nb) work instead of being formed.  It is not exactly Haar
+    distributed; the benchmark uses it only where the spectrum, not the
+    distribution of the singular vectors, matters."""
+
+    def __init__(self, N: int, seed: int, nb: int = 1024):
+        rng = np.random.default_rng(seed)
+        self.N, self.nb = N, nb
+        self.sizes = [min(nb, N - s) for s in range(0, N, nb)]
+        self.B1 = [haar_np(b, b, int(rng.integers(1 << 62))) for b in self.sizes]
+        self.B2 = [haar_np(b, b, int(rng.integers(1 << 62))) for b in self.sizes]
+        self.perm = rng.permutation(N)
+
+    def apply(self, X):
+        """M @ X for a torch float64 tensor X (N x k) on any device."""
+        import torch
+        dev = X.device
+
+        def blockdiag(Bs, Y):
+            out = torch.empty_like(Y)
+            r = 0
+            for B in Bs:
+                b = B.shape[0]
+                out[r:r + b] = torch.as_tensor(B, device=dev) @ Y[r:r + b]
+                r += b
+            return out
+
+        Y = blockdiag(self.B2, X)
+        Y = Y[torch.as_tensor(self.perm, device=dev)]
+        return blockdiag(self.B1, Y)
 
 
 def test_matrix_torch(m: int, n: int, sigma, seed_u: int = SEED_U, seed_v: int = SEED_V,
-                      device="cuda", qr_dtype=None):
-    """A = Uh diag(sigma) Vh^T built on `device` (for sizes too large for the host).
+                      device="cuda", nb: int = 1024):
+    """A = Uh diag(sigma) Vh^T (m x n, float64, column-major) built on `device`.
 
-    Returns a float64 tensor holding A in column-major order: the tensor is the
-    transpose-view of a row-major n x m buffer, so ``A.t().contiguous()`` is not
-    needed by callers that pass ``A.data_ptr()`` with lda = m.  The Haar factors
-    are drawn with torch's generator, so these matrices differ from
-    ``test_matrix_np`` for the same seeds; the sigma profile is the same.
-    ``qr_dtype`` (default float64) may be float32 to speed up synthesis of very
-    large inputs; A is then orthogonally mixed only to ~1e-6, which changes its
-    singular values by that relative amount and nothing else.
+    Uh is the first n columns of a MixedOrthogonal(m), Vh a MixedOrthogonal(n),
+    so A has exactly the singular values sigma (to rounding).  Uses only
+    matrix products on the device (no device linear-algebra library).
     """
     import torch
-    qr_dtype = qr_dtype or torch.float64
     s = torch.as_tensor(np.asarray(sigma), device=device, dtype=torch.float64)
-    Uh = _haar_torch(m, n, seed_u, device, qr_dtype).to(torch.float64)
-    Vh = _haar_torch(n, n, seed_v, device, qr_dtype).to(torch.float64)
-    A_rowmajor = (Uh * s) @ Vh.t()             # m x n, row-major
-    del Uh, Vh
-    # column-major m x n storage == row-major n x m storage of A^T
+    Mv = MixedOrthogonal(n, seed_v, nb)
+    Vt = Mv.apply(torch.eye(n, dtype=torch.float64, device=device)).t().contiguous()  # Vh^T
+    C = torch.zeros((m, n), dtype=torch.float64, device=device)
+    C[:n] = s[:, None] * Vt                       # [diag(sigma) Vh^T ; 0]
+    del Vt
+    A_rowmajor = MixedOrthogonal(m, seed_u, nb).apply(C)   # Mu [diag(sigma) Vh^T; 0]
+    del C
     return A_rowmajor.t().contiguous().t()
 
 
