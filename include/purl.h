@@ -51,9 +51,11 @@ extern "C" {
 
 /* precision modes for purl_urv_factor_ex / purl_qr */
 #define PURL_MODE_FP64 0
-/* Power-step products A Y and A^T Z on BF16 tensor cores (FP32 accumulate);
- * A V, every QR trailing update and Q formation as split-BF16 compensated
- * products; Householder panels in FP64. */
+/* Power-step products A Y and A^T Z on BF16 tensor cores with FP32
+ * accumulation (one BF16 slice per operand); A V, every QR trailing update,
+ * T factor and Q formation as exact-accumulation products of fixed-point BF16
+ * slices (2 slices in the power iteration's re-orthonormalisations, 4 in the
+ * QRs of Eqs. (5)-(6) and in A V); Householder panels in FP64. */
 #define PURL_MODE_MIXED_BF16 2
 
 /* Human-readable text for a status code (static storage). */
@@ -128,9 +130,10 @@ int purl_gemm_f64(char transa, char transb, int m, int n, int k, double alpha, c
 
 /*
  * purl_gemm_tc -- the same product on the BF16 tensor cores (tcgen05, FP32
- * accumulation in tensor memory) with `slices` in {1, 2, 3}: each FP64
+ * accumulation in tensor memory) with `slices` in {1, 2, 3} ({1..4} when
+ * exact): each FP64
  * operand is split into that many BF16 slices and the slice pairs (s, t) with
- * s + t < slices are multiplied (1, 3 or 6 BF16 products).
+ * s + t < slices are multiplied (1, 3, 6 or 10 BF16 products).
  *   exact = 0: floating slices X_0 = bf16(X), X_1 = bf16(X - X_0), ...; the
  *              accumulator's own rounding limits the result to about
  *              (k/16) 2^-23 of sum |a||b| however many slices are used.

@@ -8,7 +8,8 @@
 // scaled by a power of two and cut into slices of small integers
 // (|alpha| <= 128, exact in BF16), so every product is an integer below 2^14
 // and every partial sum of one slice-pair class over 256 of K is an integer
-// below 2^24 -- exactly representable, so the accumulator never rounds.
+// of magnitude at most (S pairs) 256 2^14 <= 2^24 for S <= 4 -- exactly
+// representable, so the accumulator never rounds.
 //
 // Per 256 of K ("chunk") the classes d = s + t (S of them) accumulate in
 // their own TMEM columns; two chunk buffers alternate so the MMA warp fills
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
       tc_fence_after();
 #pragma unroll
       for (int d = 0; d < S; ++d) {
-        const float w = d == 0 ? 1.0f : (d == 1 ? 0x1.0p-8f : 0x1.0p-16f);
+        const float w = d == 0 ? 1.0f : (d == 1 ? 0x1.0p-8f : (d == 2 ? 0x1.0p-16f : 0x1.0p-24f));
 #pragma unroll
         for (int h = 0; h < TCX_BN / 32; ++h) {
           uint32_t v[32];
@@ -352,7 +353,7 @@ int tcx_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0
   if (M <= 0 || N <= 0) return PURL_OK;
   if (K <= 0 || k_chunk <= 0 || (k_chunk % (TC_BK * TCX_KBC)) != 0 || splits != ceil_div(K, k_chunk))
     return PURL_ERR_UNSUPPORTED;
-  if (S < 1 || S > 3 || A.S < S || B.S < S || !A.scale || !B.scale) return PURL_ERR_UNSUPPORTED;
+  if (S < 1 || S > 4 || A.S < S || B.S < S || !A.scale || !B.scale) return PURL_ERR_UNSUPPORTED;
   if ((a_r0 % 8) != 0 || (b_r0 % 8) != 0) return PURL_ERR_UNSUPPORTED;
   if (ep.mode == 2 && !ep.Pd) return PURL_ERR_UNSUPPORTED;
   if (ep.mode == 0 && !ep.C) return PURL_ERR_UNSUPPORTED;
@@ -363,7 +364,8 @@ int tcx_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0
   TcView va{a_r0, a_c0}, vb{b_r0, b_c0};
   if (S == 1) return launch_tcx<1>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
   if (S == 2) return launch_tcx<2>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
-  return launch_tcx<3>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
+  if (S == 3) return launch_tcx<3>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
+  return launch_tcx<4>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
 }
 
 }  // namespace purl

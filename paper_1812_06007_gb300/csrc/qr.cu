@@ -133,8 +133,12 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
 // ------------------------------------------------------------ T factor ----
 // Sum the split-K partials of the Gram matrix V^T V and run the forward
 // column recurrence of the compact-WY T factor.  One block.
+// With tau_from_gram, tau_k is re-derived as 2 / (v_k^T v_k) from the Gram
+// matrix itself, so that each I - tau_k v_k v_k^T is orthogonal for exactly the
+// vectors the Gram matrix was formed from (used when the products see a
+// rounded copy of V).
 __global__ void __launch_bounds__(256) larft_kernel(int bw, int splits, const double *Gp,
-                                                    const double *tau, double *T) {
+                                                    const double *tau, double *T, bool tau_from_gram) {
   __shared__ double Gm[QR_B][QR_B + 1];
   __shared__ double Ts[QR_B][QR_B + 1];
   for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) {
@@ -147,6 +151,7 @@ __global__ void __launch_bounds__(256) larft_kernel(int bw, int splits, const do
   __syncthreads();
   for (int k = 0; k < bw; ++k) {
     double tk = tau[k];
+    if (tau_from_gram && tk != 0.0) tk = 2.0 / Gm[k][k];
     int i = threadIdx.x;
     double s = 0.0;
     if (i < k)
@@ -330,6 +335,49 @@ static int apply_block(int rows, int bw, int nc, double *C, int ldc, const doubl
   return gemm_f64(false, false, rows, nc, bw, -1.0, w.Vb, rows, w.W2, bw, 1.0, C, ldc, s);
 }
 
+// One panel: Householder vectors of F(j0:m, j0:j0+bw) (F points at F(j0, j0)),
+// explicit V in w.Vb (ld = rows), tau; `counter` must be 0 on entry.
+int panel_factor(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *counter, QrWork &w,
+                 cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  int P = panel_blocks(rows, di);
+  int ch = ceil_div(rows, P);
+  size_t smem = (size_t)ch * QR_B * sizeof(double);
+  if (smem > (size_t)di->max_smem_optin - 4096) return PURL_ERR_UNSUPPORTED;
+  int cap = panel_capacity(di, smem);
+  if (cap < P) return PURL_ERR_UNSUPPORTED;
+  int ldv = rows;
+  long long ldf_ll = ldf, ldv_ll = ldv;
+  void *args[] = {&rows, &bw, &ch, &Fp, &ldf_ll, &w.Vb, &ldv_ll, &taup, &w.part, &w.rowk, &counter,
+                  (void *)&di->ctrl};
+  LaunchScope ls(KC_PANEL, s, 2.0 * rows * bw * (double)bw, 16.0 * rows * bw);
+  PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel, dim3(P), dim3(PNT), args, smem, s));
+  return PURL_OK;
+}
+
+// T factor of one panel from split-K partials of its Gram matrix V^T V.
+int larft_from_gram(int bw, int splits, const double *Gp, const double *taup, double *Tp, cudaStream_t s,
+                    bool tau_from_gram) {
+  { LaunchScope ls(KC_OTHER, s); larft_kernel<<<1, 256, 0, s>>>(bw, splits, Gp, taup, Tp, tau_from_gram); }
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+int extract_v(int rows, int bw, const double *Fp, int ldf, double *Vb, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  { LaunchScope ls(KC_OTHER, s);
+    extract_v_kernel<<<grid_for((long long)rows * bw, di), 256, 0, s>>>(rows, bw, Fp, ldf, Vb, rows); }
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+int set_identity(int m, int n, double *Q, int ldq, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  { LaunchScope ls(KC_OTHER, s); set_identity_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, Q, ldq); }
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
 int qr_factor_f64(int m, int n, double *F, int ldf, QrWork &w, cudaStream_t s) {
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
@@ -341,31 +389,14 @@ int qr_factor_f64(int m, int n, double *F, int ldf, QrWork &w, cudaStream_t s) {
     int bw = min(QR_B, n - j0);
     int rows = m - j0;
     double *Fp = F + j0 + (size_t)j0 * ldf;
-    int P = panel_blocks(rows, di);
-    int ch = ceil_div(rows, P);
-    size_t smem = (size_t)ch * QR_B * sizeof(double);
-    if (smem > (size_t)di->max_smem_optin - 4096) return PURL_ERR_UNSUPPORTED;
-    int cap = panel_capacity(di, smem);
-    if (cap < P) return PURL_ERR_UNSUPPORTED;
     double *taup = w.tau + j0;
-    unsigned *cnt = w.counters + p;
-    int ldv = rows;
-    long long ldf_ll = ldf, ldv_ll = ldv;
-    void *args[] = {&rows, &bw, &ch, &Fp, &ldf_ll, &w.Vb, &ldv_ll, &taup, &w.part, &w.rowk, &cnt,
-                    (void *)&di->ctrl};
-    {
-      LaunchScope ls(KC_PANEL, s, 2.0 * rows * bw * (double)bw, 16.0 * rows * bw);
-      PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel, dim3(P), dim3(PNT),
-                                                args, smem, s));
-    }
+    PURL_TRY(panel_factor(rows, bw, Fp, ldf, taup, w.counters + p, w, s));
     // T factor from the Gram matrix V^T V
     int gs, gchunk;
     choose_splits(bw, bw, rows, di->num_sms, &gs, &gchunk);
-    if (gs > QR_MAX_SPLITS) gs = QR_MAX_SPLITS, gchunk = ceil_div(ceil_div(rows, gs), 16) * 16;
-    PURL_TRY(gemm_f64_splitk(true, false, bw, bw, rows, gs, gchunk, w.Vb, ldv, w.Vb, ldv, w.Gp, s));
+    PURL_TRY(gemm_f64_splitk(true, false, bw, bw, rows, gs, gchunk, w.Vb, rows, w.Vb, rows, w.Gp, s));
     double *Tp = w.T + (size_t)p * QR_B * QR_B;
-    { LaunchScope ls(KC_OTHER, s); larft_kernel<<<1, 256, 0, s>>>(bw, gs, w.Gp, taup, Tp); }
-    PURL_CUDA_TRY(cudaGetLastError());
+    PURL_TRY(larft_from_gram(bw, gs, w.Gp, taup, Tp, s));
     // trailing update with Q_p^T
     PURL_TRY(apply_block(rows, bw, n - j0 - bw, Fp + (size_t)bw * ldf, ldf, Tp, true, w, di, s));
   }
@@ -377,17 +408,13 @@ int qr_form_q_f64(int m, int n, const double *F, int ldf, QrWork &w, double *Q, 
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
   if (m == 0 || n == 0) return PURL_OK;
-  { LaunchScope ls(KC_OTHER, s); set_identity_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, Q, ldq); }
-  PURL_CUDA_TRY(cudaGetLastError());
+  PURL_TRY(set_identity(m, n, Q, ldq, s));
   int npan = ceil_div(n, QR_B);
   for (int p = npan - 1; p >= 0; --p) {
     int j0 = p * QR_B;
     int bw = min(QR_B, n - j0);
     int rows = m - j0;
-    { LaunchScope ls(KC_OTHER, s);
-      extract_v_kernel<<<grid_for((long long)rows * bw, di), 256, 0, s>>>(
-          rows, bw, F + j0 + (size_t)j0 * ldf, ldf, w.Vb, rows); }
-    PURL_CUDA_TRY(cudaGetLastError());
+    PURL_TRY(extract_v(rows, bw, F + j0 + (size_t)j0 * ldf, ldf, w.Vb, s));
     const double *Tp = w.T + (size_t)p * QR_B * QR_B;
     PURL_TRY(apply_block(rows, bw, n - j0, Q + j0 + (size_t)j0 * ldq, ldq, Tp, false, w, di, s));
   }

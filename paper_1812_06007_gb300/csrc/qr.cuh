@@ -21,6 +21,12 @@ struct QrWork {
 };
 
 int qr_plan(Arena &ar, int m, int n, int mode, QrWork *w);
+int panel_factor(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *counter, QrWork &w,
+                 cudaStream_t s);
+int larft_from_gram(int bw, int splits, const double *Gp, const double *taup, double *Tp, cudaStream_t s,
+                    bool tau_from_gram = false);
+int extract_v(int rows, int bw, const double *Fp, int ldf, double *Vb, cudaStream_t s);
+int set_identity(int m, int n, double *Q, int ldq, cudaStream_t s);
 int qr_factor_f64(int m, int n, double *F, int ldf, QrWork &w, cudaStream_t s);
 int qr_form_q_f64(int m, int n, const double *F, int ldf, QrWork &w, double *Q, int ldq,
                   cudaStream_t s);

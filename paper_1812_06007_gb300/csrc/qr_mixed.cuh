@@ -1,0 +1,34 @@
+// qr_mixed.cuh -- mixed-precision blocked Householder QR (internal).
+#pragma once
+
+#include "qr.cuh"
+#include "tc.cuh"
+
+namespace purl {
+
+struct QrMixWork {
+  QrWork base;       // tau, T, panel V (FP64), panel scratch, Gram partials
+  int S = 3;         // slices per operand in every product
+  int *col_exp = nullptr;  // per-column exponents of the active block's slices
+  Slices Fs;         // slices of the matrix being factored, scale = col_exp
+  Slices Qs;         // slices of the Q being formed, scale = col_exp
+  Slices Vs;         // slices of the panel's V (rows x QR_B), own column scales
+  Slices Vts;        // slices of V^T (QR_B x rows), scale per row of V
+  double *Pd = nullptr;  // split-K FP64 partials of W^T = C^T V
+  Slices W2s;        // slices of W2 = op(T) V^T C (QR_B x n), own column scales
+};
+
+int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w);
+// Work with S slices (<= the S the workspace was planned for) from now on.
+inline void qr_mixed_use_slices(QrMixWork &w, int S) {
+  w.S = S;
+  w.Fs.S = S; w.Qs.S = S; w.Vs.S = S; w.Vts.S = S; w.W2s.S = S;
+}
+
+// F (m x n, ld ldf) holds M on entry and the packed factor (R above the
+// diagonal, Householder vectors below) on exit.
+int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t s);
+// Q (m x n) from the packed factor; diag signs are NOT normalised here.
+int qr_mixed_form_q(int m, int n, const double *F, int ldf, QrMixWork &w, double *Q, int ldq, cudaStream_t s);
+
+}  // namespace purl

@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "qr.cuh"
+#include "qr_mixed.cuh"
 #include "tc.cuh"
 
 namespace purl {
@@ -46,18 +47,38 @@ const DeviceInfo *device_info() {
 }
 
 // --------------------------------------------------------- workspace ------
+// Slices per operand: the power-step products use one (plain BF16), the
+// re-orthonormalisations of the power iteration use kReorthSlices and the two
+// QRs that define V and U, R (Eqs. (5), (6)) and A V use kFinalSlices, all with
+// exact accumulation.
+constexpr int kReorthSlices = 2;
+constexpr int kFinalSlices = 4;
+
 struct UrvWork {
   double *buf[3] = {nullptr, nullptr, nullptr};  // each m x n
-  QrWork qr;
+  QrWork qr;                                     // FP64 mode
+  // mixed mode
+  QrMixWork qm;
+  Slices At1, An1, Ax, Ys, Zs, Vx;
 };
 
 static int urv_plan(Arena &ar, int m, int n, int mode, UrvWork *w) {
   size_t mn = (size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1);
   for (int i = 0; i < 3; ++i) w->buf[i] = ar.take<double>(mn);
-  return qr_plan(ar, m, n, mode, &w->qr);
+  if (mode == PURL_MODE_FP64) return qr_plan(ar, m, n, mode, &w->qr);
+  PURL_TRY(qr_mixed_plan(ar, m, n, kFinalSlices, &w->qm));
+  w->At1 = make_slices(ar.take<__nv_bfloat16>(slice_elems(n, m, 1)), n, m, 1);
+  w->An1 = make_slices(ar.take<__nv_bfloat16>(slice_elems(m, n, 1)), m, n, 1);
+  w->Ax = make_slices(ar.take<__nv_bfloat16>(slice_elems(n, m, kFinalSlices)), n, m, kFinalSlices);
+  w->Ax.scale = ar.take<int>(m > 0 ? m : 1);
+  w->Ys = make_slices(ar.take<__nv_bfloat16>(slice_elems(n, n, 1)), n, n, 1);
+  w->Zs = make_slices(ar.take<__nv_bfloat16>(slice_elems(m, n, 1)), m, n, 1);
+  w->Vx = make_slices(ar.take<__nv_bfloat16>(slice_elems(n, n, kFinalSlices)), n, n, kFinalSlices);
+  w->Vx.scale = ar.take<int>(n > 0 ? n : 1);
+  return PURL_OK;
 }
 
-static bool mode_ok(int mode) { return mode == PURL_MODE_FP64; }
+static bool mode_ok(int mode) { return mode == PURL_MODE_FP64 || mode == PURL_MODE_MIXED_BF16; }
 
 // Stream-ordered scratch: the caller's workspace, or one allocated on the stream.
 struct Scratch {
@@ -68,6 +89,7 @@ struct Scratch {
     s = stream;
     if (ws) {
       if (ws_bytes < need) return PURL_ERR_NOMEM;
+      if (((uintptr_t)ws & 255) != 0) return PURL_ERR_NOMEM;
       ptr = ws;
       return PURL_OK;
     }
@@ -81,9 +103,9 @@ struct Scratch {
   }
 };
 
-static int urv_run(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
-                   double *U, int ldu, double *R, int ldr, double *V, int ldv, int mode,
-                   UrvWork &w, cudaStream_t s) {
+static int urv_run_fp64(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                        double *U, int ldu, double *R, int ldr, double *V, int ldv, UrvWork &w,
+                        cudaStream_t s) {
   double *Y = w.buf[0], *Z = w.buf[1], *F = w.buf[2];
   PURL_TRY(launch_gaussian(seed, 0, n, n, Y, n, s));
   for (int i = 1; i <= q; ++i) {
@@ -113,6 +135,73 @@ static int urv_run(int m, int n, const double *A, int lda, int q, int reorth, ui
   PURL_TRY(qr_factor_f64(m, n, F, m, w.qr, s));
   PURL_TRY(qr_form_q_f64(m, n, F, m, w.qr, U, ldu, s));
   return qr_sign_fix(m, n, F, m, U, ldu, R, ldr, s);
+}
+
+// Mixed precision: power steps on BF16 tensor cores (one slice, FP32
+// accumulation -- they only shape the subspace), re-orthonormalisations with
+// kReorthSlices exact slices, and the QRs of Eqs. (5)-(6) plus A V with
+// kFinalSlices exact slices; Householder panels in FP64.
+static int urv_run_mixed(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                         double *U, int ldu, double *R, int ldr, double *V, int ldv, UrvWork &w,
+                         cudaStream_t s) {
+  double *Y = w.buf[0], *Z = w.buf[1], *F = w.buf[2];
+  TcEpilogue ep;
+  ep.mode = 0;
+  if (q > 0) {
+    PURL_TRY(split_slices_t(m, n, A, lda, w.At1, s));  // operand of A Y   (rows n = K, cols m = M)
+    PURL_TRY(split_slices(m, n, A, lda, w.An1, s));    // operand of A^T Z (rows m = K, cols n = M)
+  }
+  PURL_TRY(launch_gaussian(seed, 0, n, n, Y, n, s));
+  for (int i = 1; i <= q; ++i) {
+    PURL_TRY(split_slices(n, n, Y, n, w.Ys, s));
+    ep.C = F;
+    ep.ldc = m;
+    PURL_TRY(tc_gemm(w.At1, w.Ys, m, n, n, 1, ep, 1, ceil_div(n, 64) * 64, s));  // F = A Y
+    if (reorth) {
+      qr_mixed_use_slices(w.qm, kReorthSlices);
+      PURL_TRY(qr_mixed_factor(m, n, F, m, w.qm, s));
+      PURL_TRY(qr_mixed_form_q(m, n, F, m, w.qm, Z, m, s));
+      PURL_TRY(qr_sign_fix(m, n, F, m, Z, m, nullptr, 0, s));
+    } else {
+      double *t = F; F = Z; Z = t;
+    }
+    PURL_TRY(split_slices(m, n, Z, m, w.Zs, s));
+    ep.C = F;
+    ep.ldc = n;
+    PURL_TRY(tc_gemm(w.An1, w.Zs, n, n, m, 1, ep, 1, ceil_div(m, 64) * 64, s));  // F = A^T Z
+    if (reorth && i < q) {
+      qr_mixed_use_slices(w.qm, kReorthSlices);
+      PURL_TRY(qr_mixed_factor(n, n, F, n, w.qm, s));
+      PURL_TRY(qr_mixed_form_q(n, n, F, n, w.qm, Y, n, s));
+      PURL_TRY(qr_sign_fix(n, n, F, n, Y, n, nullptr, 0, s));
+    } else {
+      double *t = F; F = Y; Y = t;
+    }
+  }
+  // Eq. (5): (A^T A)^q G = V Z'
+  qr_mixed_use_slices(w.qm, kFinalSlices);
+  PURL_TRY(qr_mixed_factor(n, n, Y, n, w.qm, s));
+  PURL_TRY(qr_mixed_form_q(n, n, Y, n, w.qm, V, ldv, s));
+  PURL_TRY(qr_sign_fix(n, n, Y, n, V, ldv, nullptr, 0, s));
+  // A V with exact slices: A^T staged in Z (n x m), scale per row of A
+  PURL_TRY(transpose_f64(m, n, A, lda, Z, n, s));
+  PURL_TRY(split_exact(n, m, Z, n, w.Ax, nullptr, s));
+  PURL_TRY(split_exact(n, n, V, ldv, w.Vx, nullptr, s));
+  ep.C = F;
+  ep.ldc = m;
+  PURL_TRY(tcx_gemm_view(w.Ax, 0, 0, w.Vx, 0, 0, m, n, n, kFinalSlices, ep, 1, ceil_div(n, 256) * 256, s));
+  // Eq. (6): A V = U R
+  PURL_TRY(qr_mixed_factor(m, n, F, m, w.qm, s));
+  PURL_TRY(qr_mixed_form_q(m, n, F, m, w.qm, U, ldu, s));
+  return qr_sign_fix(m, n, F, m, U, ldu, R, ldr, s);
+}
+
+static int urv_run(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                   double *U, int ldu, double *R, int ldr, double *V, int ldv, int mode,
+                   UrvWork &w, cudaStream_t s) {
+  if (mode == PURL_MODE_MIXED_BF16)
+    return urv_run_mixed(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, w, s);
+  return urv_run_fp64(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, w, s);
 }
 
 static int check_factor_args(int m, int n, const double *A, int lda, int q, double *U, int ldu,
@@ -202,8 +291,13 @@ size_t purl_qr_workspace_bytes(int m, int n, int mode) {
   Arena ar;
   double *F = ar.take<double>((size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1));
   (void)F;
-  QrWork w;
-  if (qr_plan(ar, m, n, mode, &w) != PURL_OK) return 0;
+  if (mode == PURL_MODE_FP64) {
+    QrWork w;
+    if (qr_plan(ar, m, n, mode, &w) != PURL_OK) return 0;
+  } else {
+    QrMixWork w;
+    if (qr_mixed_plan(ar, m, n, kFinalSlices, &w) != PURL_OK) return 0;
+  }
   return ar.used;
 }
 
@@ -226,11 +320,20 @@ int purl_qr(int m, int n, const double *M, int ldm, double *Q, int ldq, double *
   ar.base = static_cast<char *>(scratch.ptr);
   ar.size = workspace ? workspace_bytes : need;
   double *F = ar.take<double>((size_t)m * n);
-  QrWork w;
-  PURL_TRY(qr_plan(ar, m, n, mode, &w));
+  if (mode == PURL_MODE_FP64) {
+    QrWork w;
+    PURL_TRY(qr_plan(ar, m, n, mode, &w));
+    if (!ar.ok) return PURL_ERR_NOMEM;
+    PURL_TRY(copy_matrix(m, n, M, ldm, F, m, stream));
+    return qr_explicit(m, n, F, m, Q, ldq, R, ldr, mode, w, stream);
+  }
+  QrMixWork w;
+  PURL_TRY(qr_mixed_plan(ar, m, n, kFinalSlices, &w));
   if (!ar.ok) return PURL_ERR_NOMEM;
   PURL_TRY(copy_matrix(m, n, M, ldm, F, m, stream));
-  return qr_explicit(m, n, F, m, Q, ldq, R, ldr, mode, w, stream);
+  PURL_TRY(qr_mixed_factor(m, n, F, m, w, stream));
+  if (Q) PURL_TRY(qr_mixed_form_q(m, n, F, m, w, Q, ldq, stream));
+  return qr_sign_fix(m, n, F, m, Q, ldq, R, ldr, stream);
 }
 
 int purl_gemm_f64(char transa, char transb, int m, int n, int k, double alpha, const double *A,
@@ -269,7 +372,7 @@ int purl_gemm_tc(char transa, char transb, int m, int n, int k, double alpha, co
   if (ldb < (brows > 1 ? brows : 1)) return -10;
   if (!C && (long long)m * n > 0) return -12;
   if (ldc < (m > 1 ? m : 1)) return -13;
-  if (slices < 1 || slices > 3) return -14;
+  if (slices < 1 || slices > (exact ? 4 : 3)) return -14;
   if ((long long)m * n == 0) return PURL_OK;
   if (!device_info()) return PURL_ERR_CUDA;
   if (k == 0) return gemm_f64(false, false, m, n, 0, 0.0, A, lda, B, ldb, beta, C, ldc, stream);

@@ -77,12 +77,14 @@ def test_tc_gemm_large_tile_grid(B):
     assert np.all(np.abs(got - ref) <= _bound(1, k) * mag)
 
 
-@pytest.mark.parametrize("S", [1, 2, 3])
+@pytest.mark.parametrize("S", [1, 2, 3, 4])
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T")])
 @pytest.mark.parametrize("m,n,k", [(128, 64, 256), (1, 1, 1), (200, 96, 130), (257, 300, 1100), (64, 40, 3000)])
 def test_tc_exact_matches_oracle(B, S, ta, tb, m, n, k):
-    # fixed-point slices: error <= 2^(-8S+1) * 2^(e_i + f_j) * k per entry, where
-    # 2^e_i > max_l |op(A)(i,l)| and 2^f_j > max_l |op(B)(l,j)|
+    # fixed-point slices: the representation error of an entry is at most
+    # 2^(-8S) of its row's (column's) scale 2^e_i > max_l |op(A)(i,l)|
+    # (2^f_j > max_l |op(B)(l,j)|); the product error is bounded by
+    # 2^(-8S+1) 2^(e_i + f_j) sqrt(k) x 4 (random signs, 4-sigma)
     rng = np.random.default_rng(m + 5 * n + 11 * k + S)
     A = rng.standard_normal((m, k) if ta == "N" else (k, m))
     Bm = rng.standard_normal((k, n) if tb == "N" else (n, k))
@@ -94,6 +96,15 @@ def test_tc_exact_matches_oracle(B, S, ta, tb, m, n, k):
     cb = 2.0 ** np.ceil(np.log2(np.abs(opB).max(axis=0) + 1e-300))
     bound = 2.0 ** (-8 * S + 1) * np.outer(ra, cb) * np.sqrt(k) * 4
     assert np.all(np.abs(got - ref) <= bound + 1e-300), (np.abs(got - ref) / bound).max()
+
+
+def test_tc_exact_four_slices_reach_fp32_and_beyond(B):
+    rng = np.random.default_rng(11)
+    A, Bm = rng.standard_normal((300, 2048)), rng.standard_normal((2048, 200))
+    ref = oracle.gemm("N", "N", A, Bm)
+    err = np.abs(_host(B.purl_gemm_tc("N", "N", _dev(A), _dev(Bm), slices=4, exact=True)) - ref).max()
+    # row/column scales 2^3 each: ~2^-32 x 64 x sqrt(2048) x few
+    assert err < 2.0 ** -32 * 64 * np.sqrt(2048) * 8, err
 
 
 def test_tc_exact_beats_the_accumulator_floor(B):
