@@ -25,27 +25,33 @@
 #include "profile.cuh"
 #include "tc.cuh"
 #include "tc_ptx.cuh"
+#include "slice_int.cuh"
 
 namespace purl {
 
 namespace {
 
 constexpr int TCX_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
-constexpr int TCX_BN = 64;
 constexpr int TCX_KBC = 4;        // k-blocks per exact chunk (4 x 64 = 256 of K)
 constexpr int TCX_GROUP = 16;
 
-template <int S>
+// S slices per operand; ALL = every slice pair (s, t) instead of s + t < S
+// (2S - 1 classes, used where the product of two sliced matrices must be
+// exact, e.g. the Gram matrix of rounded Householder vectors); BN = N tile.
+template <int S, bool ALL, int BN>
 struct TcxCfg {
+  static constexpr int CLASSES = ALL ? 2 * S - 1 : S;
   static constexpr int A_BYTES = TC_BM * TC_BK * 2;
-  static constexpr int B_BYTES = TCX_BN * TC_BK * 2;
+  static constexpr int B_BYTES = BN * TC_BK * 2;
   static constexpr int STAGE_BYTES = S * (A_BYTES + B_BYTES);
   static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
   static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
-  static constexpr int USED_COLS = 2 * S * TCX_BN;
+  static constexpr int USED_COLS = 2 * CLASSES * BN;
   static constexpr int TMEM_COLS = USED_COLS <= 128 ? 128 : (USED_COLS <= 256 ? 256 : 512);
   static_assert(STAGES >= 2, "stages");
+  static_assert(USED_COLS <= 512, "tensor memory");
+  static_assert(BN % 32 == 0, "BN");
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -61,23 +67,14 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
   lo = __fadd_rn(lo, e);
 }
 
-// x = 2^e * sum_s alpha_s 2^(-7-8s), alpha_s = integers in [-128, 128].
-__device__ __forceinline__ void write_exact_slices(double x, int e, __nv_bfloat16 *dst, long long plane, int S) {
-  double t = ldexp(x, -e) * 128.0;
-  for (int s = 0; s < S; ++s) {
-    const double a = rint(t);
-    dst[s * plane] = __double2bfloat16(a);  // exact: |a| <= 128 (<= 129 with rounding slack)
-    t = (t - a) * 256.0;
-  }
-}
-
-template <int S>
+template <int S, bool ALL, int BN>
 __global__ void __launch_bounds__(TCX_THREADS, 1)
     tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcView va,
                     TcView vb, int M, int N, int K, int k_chunk, const int *__restrict__ scA,
                     const int *__restrict__ scB, TcEpilogue ep, DeviceControl *ctrl) {
-  using Cfg = TcxCfg<S>;
+  using Cfg = TcxCfg<S, ALL, BN>;
   constexpr int STAGES = Cfg::STAGES;
+  constexpr int TCX_BN = BN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[STAGES];
@@ -163,14 +160,17 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
 #pragma unroll
         for (int s = 0; s < S; ++s) {
 #pragma unroll
-          for (int t = 0; t < S - s; ++t) {
-            const uint32_t dcol = tmem + (uint32_t)((b * S + s + t) * TCX_BN);
+          for (int t = 0; t < (ALL ? S : S - s); ++t) {
+            const int d = s + t;
+            const uint32_t dcol = tmem + (uint32_t)((b * Cfg::CLASSES + d) * TCX_BN);
+            // class d is first reached at s = max(0, d - (S-1)) (t descending from its cap)
+            const bool first = (s == (d > S - 1 ? d - (S - 1) : 0));
 #pragma unroll
             for (int k = 0; k < TC_BK / 16; ++k) {
               const uint64_t ad = sw128_desc(sa + s * Cfg::A_BYTES + k * 32);
               const uint64_t bd = sw128_desc(sb + t * Cfg::B_BYTES + k * 32);
-              // the first product of class s+t in a chunk overwrites its accumulator
-              tc_mma(dcol, ad, bd, idesc, (kin == 0 && s == 0 && k == 0) ? 0u : 1u);
+              // the first product of a class in a chunk overwrites its accumulator
+              tc_mma(dcol, ad, bd, idesc, (kin == 0 && first && k == 0) ? 0u : 1u);
             }
           }
         }
@@ -194,12 +194,12 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
       }
       tc_fence_after();
 #pragma unroll
-      for (int d = 0; d < S; ++d) {
-        const float w = d == 0 ? 1.0f : (d == 1 ? 0x1.0p-8f : (d == 2 ? 0x1.0p-16f : 0x1.0p-24f));
+      for (int d = 0; d < Cfg::CLASSES; ++d) {
+        const float w = __int_as_float((127 - 8 * d) << 23);  // 2^(-8d)
 #pragma unroll
         for (int h = 0; h < TCX_BN / 32; ++h) {
           uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)((b * S + d) * TCX_BN + h * 32), v);
+          tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)((b * Cfg::CLASSES + d) * TCX_BN + h * 32), v);
 #pragma unroll
           for (int j = 0; j < 32; ++j) two_sum_acc(hi[h * 32 + j], lo[h * 32 + j], __uint_as_float(v[j]) * w);
         }
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
             *p = x;
             if (ep.out.base) {
               __nv_bfloat16 *o = ep.out.base + row + (long long)col * ep.out.ld;
-              if (ep.out.scale) write_exact_slices(x, ep.out.scale[col], o, ep.out.plane, ep.out.S);
+              if (ep.out.scale) write_fixed_slices(x, ep.out.scale[col], o, ep.out.plane, ep.out.S);
               else write_slices(x, o, ep.out.plane, ep.out.S);
             }
           } else {
@@ -243,34 +243,33 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
 }
 
 // One block per column: exponent of the column maximum (or the given one),
-// then the exact slices of the column.
+// then the fixed-point slices of the column (integer arithmetic only).
 __global__ void __launch_bounds__(256) split_exact_kernel(int R, int Cc, const double *__restrict__ X, long long ldx,
                                                           Slices dst, const int *__restrict__ scale_from) {
-  __shared__ double red[8];
+  __shared__ unsigned long long red[8];
   __shared__ int s_e;
   for (int c = blockIdx.x; c < Cc; c += gridDim.x) {
     const double *col = X + (long long)c * ldx;
     if (scale_from) {
       if (threadIdx.x == 0) s_e = scale_from[c];
     } else {
-      double mx = 0.0;
-      for (int r = threadIdx.x; r < R; r += 256) mx = fmax(mx, fabs(col[r]));
+      unsigned long long mx = 0;
+      for (int r = threadIdx.x; r < R; r += 256) mx = max(mx, abs_bits(col[r]));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
       __syncthreads();
       if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < 8; ++w) m = fmax(m, red[w]);
-        int e = 0;
-        if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |x| < 2^e
-        s_e = e;
+        unsigned long long m = 0;
+        for (int w = 0; w < 8; ++w) m = max(m, red[w]);
+        s_e = exp_above_bits(m);
       }
     }
     __syncthreads();
     const int e = s_e;
     if (threadIdx.x == 0 && dst.scale) dst.scale[c] = e;
-    for (int r = threadIdx.x; r < R; r += 256) write_exact_slices(col[r], e, dst.base + r + (long long)c * dst.ld, dst.plane, dst.S);
+    for (int r = threadIdx.x; r < R; r += 256)
+      write_fixed_slices(col[r], e, dst.base + r + (long long)c * dst.ld, dst.plane, dst.S);
     __syncthreads();
   }
 }
@@ -297,29 +296,29 @@ __global__ void __launch_bounds__(256) col_norm_exp_kernel(int R, int Cc, const 
   }
 }
 
-template <int S>
+template <int S, bool ALL, int BN>
 int launch_tcx(const CUtensorMap &ma, const CUtensorMap &mb, TcView va, TcView vb, int M, int N, int K, int k_chunk,
                int splits, const int *scA, const int *scB, const TcEpilogue &ep, DeviceControl *ctrl,
                cudaStream_t s) {
-  using Cfg = TcxCfg<S>;
+  using Cfg = TcxCfg<S, ALL, BN>;
   static thread_local int attr_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (attr_dev != dev) {
-    if (cudaFuncSetAttribute(tcx_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) !=
+    if (cudaFuncSetAttribute(tcx_gemm_kernel<S, ALL, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) !=
         cudaSuccess)
       return PURL_ERR_CUDA;
     attr_dev = dev;
   }
-  long long tiles = (long long)ceil_div(M, TC_BM) * ceil_div(N, TCX_BN);
+  long long tiles = (long long)ceil_div(M, TC_BM) * ceil_div(N, BN);
   if (tiles > 0x7fffffffLL || splits > 65535) return PURL_ERR_UNSUPPORTED;
   double flops = 2.0 * M * (double)N * K;
   double bytes = (double)S * 2.0 * ((double)M * K + (double)N * K) +
                  (ep.mode == 0 ? 8.0 * M * N * (ep.beta != 0.0 ? 2 : 1) + (ep.out.base ? 2.0 * ep.out.S * M * N : 0)
                                : 8.0 * M * N * splits);
   LaunchScope ls(KC_GEMM_TC, s, flops, bytes);
-  tcx_gemm_kernel<S><<<dim3((unsigned)tiles, splits), TCX_THREADS, Cfg::SMEM, s>>>(ma, mb, va, vb, M, N, K, k_chunk,
-                                                                                  scA, scB, ep, ctrl);
+  tcx_gemm_kernel<S, ALL, BN><<<dim3((unsigned)tiles, splits), TCX_THREADS, Cfg::SMEM, s>>>(
+      ma, mb, va, vb, M, N, K, k_chunk, scA, scB, ep, ctrl);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
@@ -346,8 +345,8 @@ int column_norm_exponents(int R, int Cc, const double *X, long long ldx, int *e,
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
-int tcx_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0, int b_c0, int M, int N, int K, int S,
-                  const TcEpilogue &ep, int splits, int k_chunk, cudaStream_t s) {
+int tcx_gemm_view_impl(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0, int b_c0, int M, int N,
+                       int K, int S, bool all_pairs, const TcEpilogue &ep, int splits, int k_chunk, cudaStream_t s) {
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
   if (M <= 0 || N <= 0) return PURL_OK;
@@ -358,14 +357,34 @@ int tcx_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0
   if (ep.mode == 2 && !ep.Pd) return PURL_ERR_UNSUPPORTED;
   if (ep.mode == 0 && !ep.C) return PURL_ERR_UNSUPPORTED;
   if (ep.mode != 0 && ep.mode != 2) return PURL_ERR_UNSUPPORTED;
+  const int BN = all_pairs ? 32 : 64;
   CUtensorMap ma, mb;
   PURL_TRY(make_map(&ma, A, a_r0 + K, a_c0 + M, TC_BM));
-  PURL_TRY(make_map(&mb, B, b_r0 + K, b_c0 + N, TCX_BN));
+  PURL_TRY(make_map(&mb, B, b_r0 + K, b_c0 + N, BN));
   TcView va{a_r0, a_c0}, vb{b_r0, b_c0};
-  if (S == 1) return launch_tcx<1>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
-  if (S == 2) return launch_tcx<2>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
-  if (S == 3) return launch_tcx<3>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
-  return launch_tcx<4>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s);
+#define PURL_TCX(S_, ALL_, BN_) \
+  return launch_tcx<S_, ALL_, BN_>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s)
+  if (!all_pairs) {
+    if (S == 1) PURL_TCX(1, false, 64);
+    if (S == 2) PURL_TCX(2, false, 64);
+    if (S == 3) PURL_TCX(3, false, 64);
+    PURL_TCX(4, false, 64);
+  }
+  if (S == 1) PURL_TCX(1, true, 32);
+  if (S == 2) PURL_TCX(2, true, 32);
+  if (S == 3) PURL_TCX(3, true, 32);
+  PURL_TCX(4, true, 32);
+#undef PURL_TCX
+}
+
+int tcx_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0, int b_c0, int M, int N, int K, int S,
+                  const TcEpilogue &ep, int splits, int k_chunk, cudaStream_t s) {
+  return tcx_gemm_view_impl(A, a_r0, a_c0, B, b_r0, b_c0, M, N, K, S, false, ep, splits, k_chunk, s);
+}
+
+int tcx_gemm_all_pairs(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0, int b_c0, int M, int N, int K,
+                       int S, const TcEpilogue &ep, int splits, int k_chunk, cudaStream_t s) {
+  return tcx_gemm_view_impl(A, a_r0, a_c0, B, b_r0, b_c0, M, N, K, S, true, ep, splits, k_chunk, s);
 }
 
 }  // namespace purl

@@ -18,9 +18,19 @@
 //     (the slice pairs the tensor-core products drop would make a tensor-core
 //     Gram matrix miss this by ~2^-8S);
 //   * W = V^T C comes out as FP64 split-K partials, is multiplied by op(T) in
-//     FP64 and re-sliced (per-column scale) for the update C - V W2.
+//     FP64 and re-sliced (per-column scale) for the update C - V W2;
+//   * two levels of blocking: QR_B-column FP64 panels are grouped into
+//     QR_NB-column outer blocks.  Inside an outer block the panels update only
+//     the block's own columns (a slab that stays in L2); the rest of the
+//     matrix receives ONE update per outer block with the aggregated
+//     I - V T_out V^T, applied as W2^T = C^T V~ with V~ = V op(T_out) and
+//     C <- C - V W2, so the trailing matrix is streamed n / QR_NB times
+//     instead of n / QR_B times.  T_out is assembled from the panels' T_k and
+//     the exact Gram matrix of the rounded V (every slice pair).  Q is formed
+//     from the outer blocks only.
 #include "profile.cuh"
 #include "qr_mixed.cuh"
+#include "slice_int.cuh"
 
 namespace purl {
 
@@ -34,21 +44,6 @@ namespace {
 
 constexpr int kChunkAlign = 256;  // exact-accumulation chunk of the tcx engine
 
-__device__ __forceinline__ void exact_slices(double x, int e, __nv_bfloat16 *dst, long long plane, int S) {
-  double t = ldexp(x, -e) * 128.0;
-  for (int s = 0; s < S; ++s) {
-    const double a = rint(t);
-    dst[s * plane] = __double2bfloat16(a);
-    t = (t - a) * 256.0;
-  }
-}
-
-__device__ __forceinline__ int exponent_above(double mx) {
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);
-  return e;
-}
-
 // Householder vectors with v_k = 1 satisfy |v_i| <= 1 (v = x / (x_0 - beta)
 // and |x_0 - beta| >= ||x||).  Each panel's V is rounded once to the grid
 // 2^-kVGridBits (V^, written back over V), which every slicing below
@@ -57,29 +52,34 @@ __device__ __forceinline__ int exponent_above(double mx) {
 // <= 1 carries the grid).  V^ is then one matrix seen identically by V^T C,
 // by the update and by the FP64 Gram matrix that defines T.
 constexpr int kVExp = 1;
-constexpr int kVGridBits = 30;
 
+// Round each Householder vector to the grid 2^(kVExp - P), P = 7 + 8(S-1)
+// (the last digit of S slices at exponent kVExp), write V^ back over V, and
+// slice V^ naturally (exponent kVExp per column) and transposed (exponent of
+// each row's largest entry, <= kVExp, so the grid is carried exactly).
 __global__ void split_v_kernel(int rows, int bw, double *V, long long ldv, Slices vs, Slices vts) {
+  const int P = 7 + 8 * (vs.S - 1);
+  const double unit = ldexp(1.0, kVExp - P);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
     double q[QR_B];
-    double mx = 0.0;
+    unsigned long long mx = 0;
 #pragma unroll
     for (int t = 0; t < QR_B; ++t) {
       q[t] = 0.0;
       if (t < bw) {
-        q[t] = ldexp(rint(ldexp(V[i + t * ldv], kVGridBits)), -kVGridBits);
+        q[t] = (double)fixed_point(V[i + t * ldv], kVExp, P) * unit;
         V[i + t * ldv] = q[t];
-        mx = fmax(mx, fabs(q[t]));
+        mx = max(mx, abs_bits(q[t]));
       }
     }
-    const int e = exponent_above(mx);
+    const int e = exp_above_bits(mx);
     vts.scale[i] = e;
     if (i < bw) vs.scale[i] = kVExp;
 #pragma unroll
     for (int t = 0; t < QR_B; ++t)
       if (t < bw) {
-        exact_slices(q[t], kVExp, vs.base + i + (long long)t * vs.ld, vs.plane, vs.S);
-        exact_slices(q[t], e, vts.base + t + (long long)i * vts.ld, vts.plane, vts.S);
+        write_fixed_slices(q[t], kVExp, vs.base + i + (long long)t * vs.ld, vs.plane, vs.S);
+        write_fixed_slices(q[t], e, vts.base + t + (long long)i * vts.ld, vts.plane, vts.S);
       }
   }
 }
@@ -107,20 +107,87 @@ __global__ void __launch_bounds__(128) reduce_tmul_slices_kernel(int bw, int nc,
     w[l] = s;
   }
   double w2[QR_B];
-  double mx = 0.0;
+  unsigned long long mx = 0;
 #pragma unroll
   for (int r = 0; r < QR_B; ++r) {
     double t = 0.0;
 #pragma unroll
     for (int l = 0; l < QR_B; ++l) t = fma(Ts[r][l], w[l], t);
     w2[r] = t;
-    if (r < bw) mx = fmax(mx, fabs(t));
+    if (r < bw) mx = max(mx, abs_bits(t));
   }
-  const int e = exponent_above(mx);
+  const int e = exp_above_bits(mx);
   W2s.scale[c] = e;
 #pragma unroll
   for (int r = 0; r < QR_B; ++r)
-    if (r < bw) exact_slices(w2[r], e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
+    if (r < bw) write_fixed_slices(w2[r], e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
+}
+
+// Explicit rounded V of an outer block: column t (0 <= t < nbw) of the block
+// is the Householder vector of global column J0 + t, i.e. 0 above row t, 1 at
+// row t, the rounded stored entries below (rows counted from J0).
+__global__ void extract_round_v_kernel(int rows, int nbw, const double *__restrict__ F, long long ldf, double *Vo,
+                                       long long ldv, int P) {
+  const double unit = ldexp(1.0, kVExp - P);
+  const long long total = (long long)rows * nbw;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % rows), t = (int)(e / rows);
+    double v = 0.0;
+    if (i == t) v = 1.0;
+    else if (i > t) v = (double)fixed_point(F[i + (long long)t * ldf], kVExp, P) * unit;
+    Vo[i + (long long)t * ldv] = v;
+  }
+}
+
+// Slices of X^T (nbw x rows) with one exponent per row of X (rows x nbw):
+// one thread per row, two passes over the row (maximum, then digits).
+__global__ void split_rows_t_kernel(int rows, int nbw, const double *__restrict__ X, long long ldx, Slices dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
+    unsigned long long mx = 0;
+    for (int t = 0; t < nbw; ++t) mx = max(mx, abs_bits(X[i + (long long)t * ldx]));
+    const int e = exp_above_bits(mx);
+    dst.scale[i] = e;
+    for (int t = 0; t < nbw; ++t)
+      write_fixed_slices(X[i + (long long)t * ldx], e, dst.base + t + (long long)i * dst.ld, dst.plane, dst.S);
+  }
+}
+
+// W2(:, c) = sum_z Pd_z(c, :)^T (nbw entries), sliced with its own exponent.
+__global__ void reduce_slices_kernel(int nbw, int nc, int splits, const double *__restrict__ Pd, Slices W2s) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  unsigned long long mx = 0;
+  for (int r = 0; r < nbw; ++r) {
+    double v = 0.0;
+    for (int z = 0; z < splits; ++z) v += Pd[(long long)z * nc * nbw + c + (long long)r * nc];
+    mx = max(mx, abs_bits(v));
+  }
+  const int e = exp_above_bits(mx);
+  W2s.scale[c] = e;
+  for (int r = 0; r < nbw; ++r) {
+    double v = 0.0;
+    for (int z = 0; z < splits; ++z) v += Pd[(long long)z * nc * nbw + c + (long long)r * nc];
+    write_fixed_slices(v, e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
+  }
+}
+
+// G = sum of split-K partials (nbw x nbw each) into Gsum (ld nbw).
+__global__ void sum_partials_kernel(int count, int splits, const double *__restrict__ P, double *out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int z = 0; z < splits; ++z) v += P[(long long)z * count + e];
+    out[e] = v;
+  }
+}
+
+// T_out(kb:kb+bw, kb:kb+bw) = T_k (QR_B x QR_B block, ld QR_B) and zero the
+// strictly lower part of that block column.
+__global__ void place_tk_kernel(int nb_ld, int kb, int bw, const double *__restrict__ Tk, double *Tout) {
+  for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) {
+    const int i = e % bw, j = e / bw;
+    Tout[(kb + i) + (long long)(kb + j) * nb_ld] = Tk[i + j * QR_B];
+  }
 }
 
 void splits_for(int M, int N, int K, int num_sms, int *splits, int *chunk) {
@@ -172,6 +239,104 @@ int apply_block_mixed(int rows, int bw, int nc, double *Cp, int ldc, const Slice
   return tcx_gemm_view(w.Vts, 0, 0, w.W2s, 0, 0, rows, nc, bw, w.S, up, 1, kChunkAlign, s);
 }
 
+constexpr int kOuterSplits = 4;
+
+int launch_grid(long long total, int cap) {
+  long long g = (total + 255) / 256;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// Build the outer block's rounded V, its slices, its Gram matrix (exact,
+// every slice pair) and T_out from the inner T_k:
+//   T_out(0:kb, kb:kb+bw) = -T_out(0:kb, 0:kb) G(0:kb, kb:kb+bw) T_k.
+int outer_prepare(int rows, int nbw, const double *FJ, int ldf, int m, int first_panel, double *Tout, bool build_t,
+                  QrMixWork &w, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  const int P = 7 + 8 * (w.S - 1);
+  { LaunchScope ls(KC_OTHER, s, 0.0, 16.0 * rows * (double)nbw);
+    extract_round_v_kernel<<<launch_grid((long long)rows * nbw, di->num_sms * 16), 256, 0, s>>>(rows, nbw, FJ, ldf,
+                                                                                                   w.Vo, m, P); }
+  PURL_CUDA_TRY(cudaGetLastError());
+  { LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * w.S) * rows * (double)nbw);
+    split_rows_t_kernel<<<launch_grid(rows, di->num_sms * 8), 256, 0, s>>>(rows, nbw, w.Vo, m, w.Vots); }
+  PURL_CUDA_TRY(cudaGetLastError());
+  if (!build_t) return PURL_OK;
+  PURL_TRY(split_exact(rows, nbw, w.Vo, m, w.Vos, nullptr, s));
+  // exact Gram matrix of the rounded V (all slice pairs)
+  int gs, gch;
+  splits_for(nbw, nbw, rows, di->num_sms, &gs, &gch);
+  TcEpilogue g;
+  g.mode = 2;
+  g.Pd = w.Go;
+  PURL_TRY(tcx_gemm_all_pairs(w.Vos, 0, 0, w.Vos, 0, 0, nbw, nbw, rows, w.S, g, gs, gch, s));
+  { LaunchScope ls(KC_OTHER, s);
+    sum_partials_kernel<<<launch_grid((long long)nbw * nbw, 256), 256, 0, s>>>(nbw * nbw, gs, w.Go, w.Tt); }
+  PURL_CUDA_TRY(cudaGetLastError());
+  double *G = w.Tt;  // nbw x nbw, ld nbw
+  PURL_CUDA_TRY(cudaMemsetAsync(Tout, 0, sizeof(double) * QR_NB * QR_NB, s));
+  double *X = w.Go;  // scratch after the sum: kb x bw products
+  for (int kb = 0, k = 0; kb < nbw; kb += QR_B, ++k) {
+    const int bw = min(QR_B, nbw - kb);
+    const double *Tk = w.base.T + (size_t)(first_panel + k) * QR_B * QR_B;
+    { LaunchScope ls(KC_OTHER, s); place_tk_kernel<<<1, 256, 0, s>>>(QR_NB, kb, bw, Tk, Tout); }
+    PURL_CUDA_TRY(cudaGetLastError());
+    if (kb == 0) continue;
+    // X = T_out(0:kb, 0:kb) G(0:kb, kb:kb+bw);  T_out(0:kb, kb:kb+bw) = -X T_k
+    PURL_TRY(gemm_f64(false, false, kb, bw, kb, 1.0, Tout, QR_NB, G + (size_t)kb * nbw, nbw, 0.0, X, kb, s));
+    PURL_TRY(gemm_f64(false, false, kb, bw, bw, -1.0, X, kb, Tk, QR_B, 0.0, Tout + (size_t)kb * QR_NB, QR_NB, s));
+  }
+  return PURL_OK;
+}
+
+// C (rows x nc at Cp, ld ldc; slices in Cs at (r0, c0)) <- (I - V op(T_out) V^T) C
+// with V = w.Vo (rows x nbw) and its slices already prepared.
+int outer_apply(int rows, int nbw, int nc, double *Cp, int ldc, const Slices &Cs, int r0, int c0, int *cexp,
+                const double *Tout, bool trans, int m, QrMixWork &w, cudaStream_t s) {
+  if (nc <= 0 || rows <= 0) return PURL_OK;
+  const DeviceInfo *di = device_info();
+  // V~ = V T_out for Q^T C (W2^T = C^T V T_out), V T_out^T for Q C
+  const double *Top = Tout;
+  if (!trans) {
+    PURL_TRY(transpose_f64(nbw, nbw, Tout, QR_NB, w.Tt, QR_NB, s));
+    Top = w.Tt;
+  }
+  PURL_TRY(split_exact(nbw, nbw, Top, QR_NB, w.Ts, nullptr, s));
+  TcEpilogue vt;
+  vt.mode = 0;
+  vt.C = w.Vtl;
+  vt.ldc = m;
+  PURL_TRY(tcx_gemm_view(w.Vots, 0, 0, w.Ts, 0, 0, rows, nbw, nbw, w.S, vt, 1, kChunkAlign, s));
+  PURL_TRY(split_exact(rows, nbw, w.Vtl, m, w.Vtls, nullptr, s));
+  // re-slice the active block with fresh per-column exponents
+  Slices view = Cs;
+  view.base = Cs.base + r0 + (long long)c0 * Cs.ld;
+  view.scale = cexp + c0;
+  PURL_TRY(split_exact(rows, nc, Cp, ldc, view, nullptr, s));
+  // W2^T = C^T V~  (nc x nbw), FP64 split-K partials
+  int sp, ch;
+  splits_for(nc, nbw, rows, di->num_sms, &sp, &ch);
+  if (sp > kOuterSplits) {
+    ch = ceil_div(ceil_div(rows, kOuterSplits), kChunkAlign) * kChunkAlign;
+    sp = ceil_div(rows, ch);
+  }
+  TcEpilogue ep;
+  ep.mode = 2;
+  ep.Pd = w.Pdo;
+  PURL_TRY(tcx_gemm_view(Cs, r0, c0, w.Vtls, 0, 0, nc, nbw, rows, w.S, ep, sp, ch, s));
+  { LaunchScope ls(KC_SPLIT, s, 0.0, 8.0 * sp * (double)nc * nbw);
+    reduce_slices_kernel<<<ceil_div(nc, 128), 128, 0, s>>>(nbw, nc, sp, w.Pdo, w.W2o); }
+  PURL_CUDA_TRY(cudaGetLastError());
+  // C <- C - V W2
+  TcEpilogue up;
+  up.mode = 0;
+  up.alpha = -1.0;
+  up.beta = 1.0;
+  up.C = Cp;
+  up.ldc = ldc;
+  return tcx_gemm_view(w.Vots, 0, 0, w.W2o, 0, 0, rows, nc, nbw, w.S, up, 1, ceil_div(nbw, kChunkAlign) * kChunkAlign, s);
+}
+
 }  // namespace
 
 int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w) {
@@ -190,6 +355,23 @@ int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w) {
   w->Pd = ar.take<double>((size_t)QR_MAX_SPLITS * nn * QR_B);
   w->W2s = make_slices(ar.take<__nv_bfloat16>(slice_elems(QR_B, n, S)), QR_B, n, S);
   w->W2s.scale = ar.take<int>(nn);
+  const size_t nout = (size_t)ceil_div(n > 0 ? n : 1, QR_NB);
+  w->Tout = ar.take<double>(nout * QR_NB * QR_NB);
+  w->Vo = ar.take<double>(mm * QR_NB);
+  w->Vtl = ar.take<double>(mm * QR_NB);
+  w->Go = ar.take<double>((size_t)QR_MAX_SPLITS * QR_NB * QR_NB);
+  w->Tt = ar.take<double>((size_t)QR_NB * QR_NB);
+  w->Pdo = ar.take<double>((size_t)kOuterSplits * nn * QR_NB);
+  w->Vos = make_slices(ar.take<__nv_bfloat16>(slice_elems(m, QR_NB, S)), m, QR_NB, S);
+  w->Vos.scale = ar.take<int>(QR_NB);
+  w->Vots = make_slices(ar.take<__nv_bfloat16>(slice_elems(QR_NB, m, S)), QR_NB, m, S);
+  w->Vots.scale = ar.take<int>(mm);
+  w->Vtls = make_slices(ar.take<__nv_bfloat16>(slice_elems(m, QR_NB, S)), m, QR_NB, S);
+  w->Vtls.scale = ar.take<int>(QR_NB);
+  w->Ts = make_slices(ar.take<__nv_bfloat16>(slice_elems(QR_NB, QR_NB, S)), QR_NB, QR_NB, S);
+  w->Ts.scale = ar.take<int>(QR_NB);
+  w->W2o = make_slices(ar.take<__nv_bfloat16>(slice_elems(QR_NB, n, S)), QR_NB, n, S);
+  w->W2o.scale = ar.take<int>(nn);
   return PURL_OK;
 }
 
@@ -197,22 +379,33 @@ int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
   if (n == 0) return PURL_OK;
-  int npan = ceil_div(n, QR_B);
+  const int npan = ceil_div(n, QR_B);
   PURL_CUDA_TRY(cudaMemsetAsync(w.base.counters, 0, sizeof(unsigned) * npan, s));
-  for (int p = 0; p < npan; ++p) {
-    const int j0 = p * QR_B, bw = min(QR_B, n - j0), rows = m - j0, nc = n - j0 - bw;
-    double *Fp = F + j0 + (size_t)j0 * ldf;
-    double *taup = w.base.tau + j0;
-    PURL_TRY(panel_factor(rows, bw, Fp, ldf, taup, w.base.counters + p, w.base, s));
-    PURL_TRY(slice_panel(rows, bw, w, s));
-    // T from the FP64 Gram matrix of the rounded V^ (exact to FP64 rounding)
-    int gs, gch;
-    choose_splits(bw, bw, rows, di->num_sms, &gs, &gch);
-    PURL_TRY(gemm_f64_splitk(true, false, bw, bw, rows, gs, gch, w.base.Vb, rows, w.base.Vb, rows, w.base.Gp, s));
-    double *Tp = w.base.T + (size_t)p * QR_B * QR_B;
-    PURL_TRY(larft_from_gram(bw, gs, w.base.Gp, taup, Tp, s, true));
-    PURL_TRY(apply_block_mixed(rows, bw, nc, Fp + (size_t)bw * ldf, ldf, w.Fs, j0, j0 + bw, w.col_exp, Tp,
-                               true, w, s));
+  for (int J0 = 0, ob = 0; J0 < n; J0 += QR_NB, ++ob) {
+    const int nbw = min(QR_NB, n - J0), rows = m - J0, nc_out = n - J0 - nbw;
+    // inner panels, their updates confined to the outer block's columns
+    for (int j0 = J0; j0 < J0 + nbw; j0 += QR_B) {
+      const int p = j0 / QR_B, bw = min(QR_B, J0 + nbw - j0), rj = m - j0;
+      const int nc_in = J0 + nbw - j0 - bw;
+      double *Fp = F + j0 + (size_t)j0 * ldf;
+      double *taup = w.base.tau + j0;
+      PURL_TRY(panel_factor(rj, bw, Fp, ldf, taup, w.base.counters + p, w.base, s));
+      PURL_TRY(slice_panel(rj, bw, w, s));
+      // T_k from the FP64 Gram matrix of the rounded V^ (exact to FP64 rounding)
+      int gs, gch;
+      choose_splits(bw, bw, rj, di->num_sms, &gs, &gch);
+      PURL_TRY(gemm_f64_splitk(true, false, bw, bw, rj, gs, gch, w.base.Vb, rj, w.base.Vb, rj, w.base.Gp, s));
+      double *Tp = w.base.T + (size_t)p * QR_B * QR_B;
+      PURL_TRY(larft_from_gram(bw, gs, w.base.Gp, taup, Tp, s, true));
+      PURL_TRY(apply_block_mixed(rj, bw, nc_in, Fp + (size_t)bw * ldf, ldf, w.Fs, j0, j0 + bw, w.col_exp, Tp, true,
+                                 w, s));
+    }
+    // one aggregated update of everything to the right of the outer block
+    double *Tout = w.Tout + (size_t)ob * QR_NB * QR_NB;
+    PURL_TRY(outer_prepare(rows, nbw, F + J0 + (size_t)J0 * ldf, ldf, m, J0 / QR_B, Tout, true, w, s));
+    if (nc_out > 0)
+      PURL_TRY(outer_apply(rows, nbw, nc_out, F + J0 + (size_t)(J0 + nbw) * ldf, ldf, w.Fs, J0, J0 + nbw, w.col_exp,
+                           Tout, true, m, w, s));
   }
   return PURL_OK;
 }
@@ -222,14 +415,13 @@ int qr_mixed_form_q(int m, int n, const double *F, int ldf, QrMixWork &w, double
   if (!di) return PURL_ERR_CUDA;
   if (m == 0 || n == 0) return PURL_OK;
   PURL_TRY(set_identity(m, n, Q, ldq, s));
-  int npan = ceil_div(n, QR_B);
-  for (int p = npan - 1; p >= 0; --p) {
-    const int j0 = p * QR_B, bw = min(QR_B, n - j0), rows = m - j0;
-    PURL_TRY(extract_v(rows, bw, F + j0 + (size_t)j0 * ldf, ldf, w.base.Vb, s));
-    PURL_TRY(slice_panel(rows, bw, w, s));
-    const double *Tp = w.base.T + (size_t)p * QR_B * QR_B;
-    PURL_TRY(apply_block_mixed(rows, bw, n - j0, Q + j0 + (size_t)j0 * ldq, ldq, w.Qs, j0, j0, w.col_exp, Tp,
-                               false, w, s));
+  const int nout = ceil_div(n, QR_NB);
+  for (int ob = nout - 1; ob >= 0; --ob) {
+    const int J0 = ob * QR_NB, nbw = min(QR_NB, n - J0), rows = m - J0;
+    const double *Tout = w.Tout + (size_t)ob * QR_NB * QR_NB;
+    PURL_TRY(outer_prepare(rows, nbw, F + J0 + (size_t)J0 * ldf, ldf, m, J0 / QR_B, nullptr, false, w, s));
+    PURL_TRY(outer_apply(rows, nbw, n - J0, Q + J0 + (size_t)J0 * ldq, ldq, w.Qs, J0, J0, w.col_exp, Tout, false, m,
+                         w, s));
   }
   return PURL_OK;
 }

@@ -1,0 +1,72 @@
+// slice_int.cuh -- fixed-point BF16 slicing of FP64 values with integer arithmetic only.
+//
+// GB300's FP64 pipe does about two operations per clock per SM, so slicing
+// with FP64 arithmetic (scale, round, subtract per slice) made the slicing
+// passes slower than the products they feed.  Here an FP64 value x with
+// |x| < 2^e becomes the integer N = round(x 2^(P-e)), P = 7 + 8(S-1),
+// straight from its IEEE bits, and N is cut into S balanced digits
+//   N = d_0 2^(8(S-1)) + d_1 2^(8(S-2)) + ... + d_{S-1},
+//   d_1..d_{S-1} in [-128, 127], d_0 in [-128, 128],
+// each of which is written as an exact BF16 (at most 8 significant bits) by
+// assembling its bit pattern.  x is then carried to 2^(e-P-1) (half a unit
+// of the last digit), i.e. 2^-8S of the scale 2^e.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace purl {
+
+// Exponent e with |x| < 2^e for the largest |x| given as its IEEE bits with the
+// sign cleared (0 for zero or subnormal maxima).
+__device__ __forceinline__ int exp_above_bits(unsigned long long absbits) {
+  const int E = (int)(absbits >> 52);
+  return E == 0 ? 0 : E - 1022;
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
+}
+
+// round(x 2^(P - e)) for |x| < 2^e (ties away from zero), from the bits of x.
+__device__ __forceinline__ long long fixed_point(double x, int e, int P) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return 0;  // zero or subnormal: below every scale used here
+  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const int sh = E - 1075 + P - e;  // x = mant 2^(E-1075)
+  long long n;
+  if (sh >= 0) {
+    n = sh < 11 ? (long long)(mant << sh) : 0;  // |x| < 2^e keeps this below 2^P
+  } else {
+    const int r = -sh;
+    n = r > 54 ? 0 : (long long)((mant + (1ULL << (r - 1))) >> r);
+  }
+  return (b >> 63) ? -n : n;
+}
+
+// Exact BF16 bit pattern of a small integer |d| <= 256.
+__device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
+  if (d == 0) return 0;
+  const unsigned sgn = d < 0 ? 0x8000u : 0u;
+  const unsigned a = (unsigned)(d < 0 ? -d : d);
+  const int msb = 31 - __clz(a);
+  const unsigned mant = (a << (7 - msb)) & 0x7Fu;
+  return (unsigned short)(sgn | ((unsigned)(127 + msb) << 7) | mant);
+}
+
+// Write the S digits of x (|x| < 2^e) as BF16 slices: slice s at dst[s * plane].
+__device__ __forceinline__ void write_fixed_slices(double x, int e, __nv_bfloat16 *dst, long long plane, int S) {
+  long long n = fixed_point(x, e, 7 + 8 * (S - 1));
+  unsigned short digit[4];
+  for (int s = S - 1; s >= 1; --s) {
+    const long long d = ((n + 128) & 255) - 128;
+    digit[s] = bf16_bits_of_int((int)d);
+    n = (n - d) >> 8;
+  }
+  digit[0] = bf16_bits_of_int((int)n);
+  unsigned short *out = reinterpret_cast<unsigned short *>(dst);
+  for (int s = 0; s < S; ++s) out[s * plane] = digit[s];
+}
+
+}  // namespace purl

@@ -71,6 +71,11 @@ int column_norm_exponents(int R, int Cc, const double *X, long long ldx, int *e,
 // slices out) or mode 2 (FP64 split-K partials at Pd + z*M*N).
 int tcx_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0, int b_c0, int M, int N,
                   int K, int S, const TcEpilogue &ep, int splits, int k_chunk, cudaStream_t s);
+// Same with every slice pair (s, t), s, t < S (2S - 1 exact classes, N tile
+// 32): the exact product of the two sliced matrices, up to FP64 rounding of
+// the result.  Used for Gram matrices that must match the sliced operands.
+int tcx_gemm_all_pairs(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0, int b_c0, int M, int N,
+                       int K, int S, const TcEpilogue &ep, int splits, int k_chunk, cudaStream_t s);
 
 // FP64 -> S BF16 slices.  split_slices: same orientation (dst is R x Cc);
 // split_slices_t: transposed (dst is Cc x R).
