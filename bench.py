@@ -237,6 +237,7 @@ def run_ours(a):
     launches = B.purl_launch_count() - launches0
     ms_total = e0.elapsed_time(e1)
     prof = B.purl_profile_read() if not a.no_profile else None
+    prof_named = B.purl_profile_read_named() if not a.no_profile else None
     B.purl_profile_enable(False)
     if world > 1:
         t = torch.tensor([ms_total], device=dev)
@@ -284,6 +285,9 @@ def run_ours(a):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "kernels": prof,
+        "kernels_by_name": ({k: {"launches": v["launches"], "ms_per_step": v["ms"] / a.steps}
+                             for k, v in sorted(prof_named.items(), key=lambda kv: -kv[1]["ms"])}
+                            if prof_named else None),
     }
     print(json.dumps(line), flush=True)
     if world > 1:

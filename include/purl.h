@@ -186,6 +186,8 @@ void purl_profile_enable(int on);
 void purl_profile_reset(void);
 int purl_profile_read(int cls, long long *launches, double *ms, double *flops, double *bytes);
 const char *purl_profile_class_name(int cls);
+/* The same totals per kernel name (index 0, 1, ... until -1 is returned). */
+int purl_profile_read_named(int index, char *name, int name_len, long long *launches, double *ms);
 
 #ifdef __cplusplus
 }

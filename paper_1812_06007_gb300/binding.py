@@ -49,6 +49,8 @@ SIGNATURES = {
     "purl_profile_read": (_i, [_i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_d),
                                ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "purl_profile_class_name": (ctypes.c_char_p, [_i]),
+    "purl_profile_read_named": (_i, [_i, ctypes.c_char_p, _i, ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(_d)]),
 }
 
 _lock = threading.Lock()
@@ -261,4 +263,19 @@ def purl_profile_read() -> dict:
         ms, fl, by = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
         lib().purl_profile_read(cls, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by))
         out[name] = {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
+    return out
+
+
+def purl_profile_read_named() -> dict:
+    """{kernel name: {launches, ms}} since the last reset (synchronises)."""
+    out = {}
+    i = 0
+    while True:
+        buf = ctypes.create_string_buffer(128)
+        n = ctypes.c_longlong(0)
+        ms = ctypes.c_double(0)
+        if lib().purl_profile_read_named(i, buf, 128, ctypes.byref(n), ctypes.byref(ms)) != 0:
+            break
+        out[buf.value.decode()] = {"launches": n.value, "ms": ms.value}
+        i += 1
     return out

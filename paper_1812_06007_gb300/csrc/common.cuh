@@ -42,8 +42,8 @@ struct DeviceInfo {
 const DeviceInfo *device_info();
 
 // Spin budget of a device-side wait: number of polls before giving up
-// (each poll sleeps ~64-128 ns, so this is on the order of a second or more).
-constexpr long long kSpinLimit = 1LL << 24;
+// (each poll is an L2 round trip of ~0.5-1 us, so this is several seconds).
+constexpr long long kSpinLimit = 1LL << 23;
 
 // ------------------------------------------------------ grid barrier ------
 // Barrier among the `nblocks` co-resident blocks of a cooperative launch.
@@ -71,7 +71,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target,
         ok = 0;
         break;
       }
-      __nanosleep(64);
     }
     __threadfence();
     s_ok = ok;

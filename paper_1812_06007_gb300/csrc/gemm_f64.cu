@@ -129,7 +129,7 @@ int launch_cfg(bool ta, bool tb, int m, int n, int k, int splits, int k_chunk, d
   if (grid.y > 65535 || grid.z > 65535) return PURL_ERR_UNSUPPORTED;
   double flops = 2.0 * m * n * (double)k;
   double bytes = 8.0 * ((double)m * k + (double)k * n + (double)m * n * (beta != 0.0 ? 2 : 1));
-  LaunchScope ls(KC_GEMM_F64, s, flops, bytes);
+  LaunchScope ls(KC_GEMM_F64, s, flops, bytes, "gemm_f64_kernel");
 #define PURL_GEMM_CASE(TA_, TB_)                                                               \
   if (ta == TA_ && tb == TB_) {                                                                \
     gemm_f64_kernel<BM, BN, TM, TN, TA_, TB_><<<grid, NT, 0, s>>>(                              \

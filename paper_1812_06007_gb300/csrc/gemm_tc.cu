@@ -21,6 +21,7 @@
 #include "profile.cuh"
 #include "tc.cuh"
 #include "tc_ptx.cuh"
+#include "slice_int.cuh"
 
 namespace purl {
 
@@ -161,9 +162,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int j = 0; j < 32; ++j) {
               const int col = n0 + c0 + j;
               if (col < N) {
-                const double acc = (double)__uint_as_float(v[j]);
+                const double acc = scaled_float_to_double(__uint_as_float(v[j]), 0);
                 double *p = ep.C + row + (long long)col * ep.ldc;
-                const double x = (ep.beta == 0.0) ? ep.alpha * acc : fma(ep.alpha, acc, ep.beta * *p);
+                const double x = (ep.beta == 0.0 && ep.alpha == 1.0)
+                                     ? acc
+                                     : ((ep.beta == 0.0) ? ep.alpha * acc : fma(ep.alpha, acc, ep.beta * *p));
                 *p = x;
                 if (ep.out.base)
                   write_slices(x, ep.out.base + row + (long long)col * ep.out.ld, ep.out.plane, ep.out.S);
@@ -241,7 +244,7 @@ int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcView va, TcView vb
                  (ep.mode == 0 ? 8.0 * M * N * (ep.beta != 0.0 ? 2 : 1) + (ep.out.base ? 2.0 * ep.out.S * M * N : 0)
                                : 4.0 * M * N * splits);
   (void)prods;
-  LaunchScope ls(KC_GEMM_TC, s, flops, bytes);
+  LaunchScope ls(KC_GEMM_TC, s, flops, bytes, ep.tag ? ep.tag : "tc_gemm_kernel");
   tc_gemm_kernel<BN, S><<<grid, TC_THREADS, Cfg::SMEM, s>>>(ma, mb, va, vb, M, N, K, k_chunk, ep, ctrl);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
@@ -287,7 +290,7 @@ int split_slices(int R, int Cc, const double *X, long long ldx, Slices dst, cuda
   if (total == 0) return PURL_OK;
   long long g = (total + 255) / 256;
   if (g > (long long)di->num_sms * 16) g = (long long)di->num_sms * 16;
-  LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * dst.S) * total);
+  LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * dst.S) * total, "split_kernel");
   split_kernel<<<(int)g, 256, 0, s>>>(R, Cc, X, ldx, dst);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
@@ -296,7 +299,7 @@ int split_slices_t(int R, int Cc, const double *X, long long ldx, Slices dst, cu
   if ((long long)R * Cc == 0) return PURL_OK;
   dim3 grid(ceil_div(R, 32), ceil_div(Cc, 32));
   if (grid.y > 65535) return PURL_ERR_UNSUPPORTED;
-  LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc);
+  LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc, "split_t_kernel");
   split_t_kernel<<<grid, dim3(32, 8), 0, s>>>(R, Cc, X, ldx, dst);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }

@@ -31,7 +31,10 @@ namespace purl {
 
 namespace {
 
-constexpr int TCX_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+// warp 0 TMA, warp 1 MMA, warps 2-9 epilogue: two warps per 32-lane quadrant
+// of tensor memory, each draining half of the tile's columns
+constexpr int TCX_THREADS = 320;
+constexpr int TCX_EPI_WARPS = 8;
 constexpr int TCX_KBC = 4;        // k-blocks per exact chunk (4 x 64 = 256 of K)
 constexpr int TCX_GROUP = 16;
 
@@ -70,7 +73,7 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
 template <int S, bool ALL, int BN>
 __global__ void __launch_bounds__(TCX_THREADS, 1)
     tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcView va,
-                    TcView vb, int M, int N, int K, int k_chunk, const int *__restrict__ scA,
+                    TcView vb, int M, int N, int K, int k_chunk, int splits, const int *__restrict__ scA,
                     const int *__restrict__ scB, TcEpilogue ep, DeviceControl *ctrl) {
   using Cfg = TcxCfg<S, ALL, BN>;
   constexpr int STAGES = Cfg::STAGES;
@@ -87,16 +90,22 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_m = (M + TC_BM - 1) / TC_BM, tiles_n = (N + TCX_BN - 1) / TCX_BN;
-  const int pid = blockIdx.x;
+  const int tiles = tiles_m * tiles_n;
+  const long long total = (long long)tiles * splits;
   const int per_group = TCX_GROUP * tiles_n;
-  const int first_m = (pid / per_group) * TCX_GROUP;
-  const int gsize = min(tiles_m - first_m, TCX_GROUP);
-  const int m0 = (first_m + (pid % per_group) % gsize) * TC_BM;
-  const int n0 = ((pid % per_group) / gsize) * TCX_BN;
-  const int kb0 = blockIdx.y * k_chunk;
-  const int kend = min(K, kb0 + k_chunk);
-  const int nkb = (kend - kb0 + TC_BK - 1) / TC_BK;
-  const int nch = (nkb + TCX_KBC - 1) / TCX_KBC;
+
+  // Persistent: this block handles work items blockIdx.x, blockIdx.x + gridDim.x, ...
+  // (work = split * tiles + tile).  Every role walks the same sequence.
+  auto work_geometry = [&](long long work, int &m0, int &n0, int &kb0, int &nkb) {
+    const int z = (int)(work / tiles), pid = (int)(work % tiles);
+    const int first_m = (pid / per_group) * TCX_GROUP;
+    const int gsize = min(tiles_m - first_m, TCX_GROUP);
+    m0 = (first_m + (pid % per_group) % gsize) * TC_BM;
+    n0 = ((pid % per_group) / gsize) * TCX_BN;
+    kb0 = z * k_chunk;
+    const int kend = min(K, kb0 + k_chunk);
+    nkb = (kend - kb0 + TC_BK - 1) / TC_BK;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -105,7 +114,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull_bar[b], 1);
-      mbar_init(&tempty_bar[b], 4);
+      mbar_init(&tempty_bar[b], TCX_EPI_WARPS);
     }
     mbar_init(&done_bar, 1);
     s_abort = 0;
@@ -124,109 +133,171 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int st = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-        if (!mbar_wait(&empty_bar[st], ph ^ 1u, ctrl, &s_abort)) break;
-        mbar_arrive_expect_tx(&full_bar[st], (uint32_t)Cfg::STAGE_BYTES);
-        uint8_t *sa = smem + (size_t)st * Cfg::STAGE_BYTES;
-        uint8_t *sb = sa + S * Cfg::A_BYTES;
-        const int kx = kb0 + kb * TC_BK;
+      long long kt = 0;  // k-blocks issued so far (stage ring position)
+      bool stop = false;
+      for (long long work = blockIdx.x; work < total && !stop; work += gridDim.x) {
+        int m0, n0, kb0, nkb;
+        work_geometry(work, m0, n0, kb0, nkb);
+        for (int kb = 0; kb < nkb; ++kb, ++kt) {
+          const int st = (int)(kt % STAGES);
+          const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+          if (!mbar_wait(&empty_bar[st], ph ^ 1u, ctrl, &s_abort)) { stop = true; break; }
+          mbar_arrive_expect_tx(&full_bar[st], (uint32_t)Cfg::STAGE_BYTES);
+          uint8_t *sa = smem + (size_t)st * Cfg::STAGE_BYTES;
+          uint8_t *sb = sa + S * Cfg::A_BYTES;
+          const int kx = kb0 + kb * TC_BK;
 #pragma unroll
-        for (int s = 0; s < S; ++s) tma_load_3d(sa + s * Cfg::A_BYTES, &tmA, &full_bar[st], va.r0 + kx, va.c0 + m0, s);
+          for (int s = 0; s < S; ++s) tma_load_3d(sa + s * Cfg::A_BYTES, &tmA, &full_bar[st], va.r0 + kx, va.c0 + m0, s);
 #pragma unroll
-        for (int s = 0; s < S; ++s) tma_load_3d(sb + s * Cfg::B_BYTES, &tmB, &full_bar[st], vb.r0 + kx, vb.c0 + n0, s);
-        issued = kb + 1;
+          for (int s = 0; s < S; ++s) tma_load_3d(sb + s * Cfg::B_BYTES, &tmB, &full_bar[st], vb.r0 + kx, vb.c0 + n0, s);
+        }
       }
-      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-        mbar_wait(&full_bar[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, ctrl, &s_abort, false);
+      // never leave the block with copies in flight: the last use of every stage
+      // must have landed (bounded; normally already true)
+      for (long long k = (kt > STAGES ? kt - STAGES : 0); k < kt; ++k)
+        mbar_wait(&full_bar[k % STAGES], (uint32_t)(k / STAGES) & 1u, ctrl, &s_abort, false);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16(TC_BM, TCX_BN);
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int c = kb / TCX_KBC, b = c & 1, kin = kb % TCX_KBC;
-        if (kin == 0) {
-          if (!mbar_wait(&tempty_bar[b], ((uint32_t)(c >> 1) & 1u) ^ 1u, ctrl, &s_abort)) break;
+      long long kt = 0, ct = 0;  // k-block and chunk counters across work items
+      bool stop = false;
+      for (long long work = blockIdx.x; work < total && !stop; work += gridDim.x) {
+        int m0, n0, kb0, nkb;
+        work_geometry(work, m0, n0, kb0, nkb);
+        for (int kb = 0; kb < nkb; ++kb, ++kt) {
+          const int kin = kb % TCX_KBC, b = (int)(ct & 1);
+          if (kin == 0) {
+            if (!mbar_wait(&tempty_bar[b], ((uint32_t)(ct >> 1) & 1u) ^ 1u, ctrl, &s_abort)) { stop = true; break; }
+            tc_fence_after();
+          }
+          const int st = (int)(kt % STAGES);
+          const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+          if (!mbar_wait(&full_bar[st], ph, ctrl, &s_abort)) { stop = true; break; }
           tc_fence_after();
-        }
-        const int st = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-        if (!mbar_wait(&full_bar[st], ph, ctrl, &s_abort)) break;
-        tc_fence_after();
-        const uint32_t sa = smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
-        const uint32_t sb = sa + S * Cfg::A_BYTES;
+          const uint32_t sa = smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
+          const uint32_t sb = sa + S * Cfg::A_BYTES;
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
+          for (int s = 0; s < S; ++s) {
 #pragma unroll
-          for (int t = 0; t < (ALL ? S : S - s); ++t) {
-            const int d = s + t;
-            const uint32_t dcol = tmem + (uint32_t)((b * Cfg::CLASSES + d) * TCX_BN);
-            // class d is first reached at s = max(0, d - (S-1)) (t descending from its cap)
-            const bool first = (s == (d > S - 1 ? d - (S - 1) : 0));
+            for (int t = 0; t < (ALL ? S : S - s); ++t) {
+              const int d = s + t;
+              const uint32_t dcol = tmem + (uint32_t)((b * Cfg::CLASSES + d) * TCX_BN);
+              // class d is first reached at s = max(0, d - (S-1))
+              const bool first = (s == (d > S - 1 ? d - (S - 1) : 0));
 #pragma unroll
-            for (int k = 0; k < TC_BK / 16; ++k) {
-              const uint64_t ad = sw128_desc(sa + s * Cfg::A_BYTES + k * 32);
-              const uint64_t bd = sw128_desc(sb + t * Cfg::B_BYTES + k * 32);
-              // the first product of a class in a chunk overwrites its accumulator
-              tc_mma(dcol, ad, bd, idesc, (kin == 0 && first && k == 0) ? 0u : 1u);
+              for (int k = 0; k < TC_BK / 16; ++k) {
+                const uint64_t ad = sw128_desc(sa + s * Cfg::A_BYTES + k * 32);
+                const uint64_t bd = sw128_desc(sb + t * Cfg::B_BYTES + k * 32);
+                // the first product of a class in a chunk overwrites its accumulator
+                tc_mma(dcol, ad, bd, idesc, (kin == 0 && first && k == 0) ? 0u : 1u);
+              }
             }
           }
+          tc_commit(&empty_bar[st]);
+          if (kin == TCX_KBC - 1 || kb == nkb - 1) {
+            tc_commit(&tfull_bar[b]);
+            ++ct;
+          }
         }
-        tc_commit(&empty_bar[st]);
-        if (kin == TCX_KBC - 1 || kb == nkb - 1) tc_commit(&tfull_bar[b]);
       }
       tc_commit(&done_bar);
     }
   } else {
-    // ---------------- epilogue: drain chunks into double-FP32 sums ----------------
+    // ---------------- epilogue: drain chunks into double-FP32 sums, then write ----------------
+    constexpr int HC = TCX_BN / 2;  // columns per epilogue warp
     const int lane_base = 32 * (warp & 3);
-    float hi[TCX_BN], lo[TCX_BN];
-#pragma unroll
-    for (int j = 0; j < TCX_BN; ++j) hi[j] = lo[j] = 0.0f;
+    const int cbase = ((warp - 2) >> 2) * HC;  // which half of the columns
+    long long ct = 0;
     bool ok = true;
-    for (int c = 0; c < nch; ++c) {
-      const int b = c & 1;
-      if (!mbar_wait(&tfull_bar[b], (uint32_t)(c >> 1) & 1u, ctrl, &s_abort)) {
-        ok = false;
-        break;
+    for (long long work = blockIdx.x; work < total && ok; work += gridDim.x) {
+      int m0, n0, kb0, nkb;
+      work_geometry(work, m0, n0, kb0, nkb);
+      const int nch = (nkb + TCX_KBC - 1) / TCX_KBC;
+      const bool reads_c = (ep.mode == 0 && ep.beta != 0.0);
+      const int row = m0 + lane_base + lane;
+      if (reads_c && row < M) {
+        // pull this row's part of the C tile into L2 while the products run
+        for (int j = 0; j < HC; ++j)
+          if (n0 + cbase + j < N)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ep.C + row + (long long)(n0 + cbase + j) * ep.ldc));
       }
-      tc_fence_after();
+      float hi[HC], lo[HC];
 #pragma unroll
-      for (int d = 0; d < Cfg::CLASSES; ++d) {
-        const float w = __int_as_float((127 - 8 * d) << 23);  // 2^(-8d)
-#pragma unroll
-        for (int h = 0; h < TCX_BN / 32; ++h) {
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)((b * Cfg::CLASSES + d) * TCX_BN + h * 32), v);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) two_sum_acc(hi[h * 32 + j], lo[h * 32 + j], __uint_as_float(v[j]) * w);
+      for (int j = 0; j < HC; ++j) hi[j] = lo[j] = 0.0f;
+      for (int c = 0; c < nch; ++c, ++ct) {
+        const int b = (int)(ct & 1);
+        if (!mbar_wait(&tfull_bar[b], (uint32_t)(ct >> 1) & 1u, ctrl, &s_abort)) {
+          ok = false;
+          break;
         }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty_bar[b]);
-    }
-    const int row = m0 + lane_base + lane;
-    if (ok && nkb > 0 && row < M) {
-      const int ea = scA[va.c0 + row];
+        tc_fence_after();
 #pragma unroll
-      for (int j = 0; j < TCX_BN; ++j) {
-        const int col = n0 + j;
-        if (col < N) {
-          const double val = ldexp((double)hi[j] + (double)lo[j], ea + scB[vb.c0 + col] - 14);
-          if (ep.mode == 0) {
-            double *p = ep.C + row + (long long)col * ep.ldc;
-            const double x = (ep.beta == 0.0) ? ep.alpha * val : fma(ep.alpha, val, ep.beta * *p);
-            *p = x;
-            if (ep.out.base) {
-              __nv_bfloat16 *o = ep.out.base + row + (long long)col * ep.out.ld;
-              if (ep.out.scale) write_fixed_slices(x, ep.out.scale[col], o, ep.out.plane, ep.out.S);
-              else write_slices(x, o, ep.out.plane, ep.out.S);
+        for (int d = 0; d < Cfg::CLASSES; ++d) {
+          const float w = __int_as_float((127 - 8 * d) << 23);  // 2^(-8d)
+          const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)((b * Cfg::CLASSES + d) * TCX_BN + cbase);
+          if constexpr (HC >= 32) {
+#pragma unroll
+            for (int h = 0; h < HC / 32; ++h) {
+              uint32_t v[32];
+              tmem_ld32(taddr + (uint32_t)(h * 32), v);
+#pragma unroll
+              for (int j = 0; j < 32; ++j) two_sum_acc(hi[h * 32 + j], lo[h * 32 + j], __uint_as_float(v[j]) * w);
             }
           } else {
-            ep.Pd[(long long)blockIdx.y * M * N + row + (long long)col * M] = val;
+            static_assert(HC == 16, "half tile of 16 or a multiple of 32 columns");
+            uint32_t v[16];
+            tmem_ld16(taddr, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) two_sum_acc(hi[j], lo[j], __uint_as_float(v[j]) * w);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty_bar[b]);
+      }
+      if (ok && nkb > 0 && row < M) {
+        const int ea = scA[va.c0 + row];
+        // the common updates C = D and C = C - D take one or two FP64 adds;
+        // hi and lo become exact doubles through integer bit assembly
+        const bool plain = (ep.alpha == 1.0 && ep.beta == 0.0);
+        const bool subtract = (ep.alpha == -1.0 && ep.beta == 1.0);
+        const int z = (int)(work / tiles);
+        constexpr int BATCH = 8;  // independent loads of C kept in flight
+#pragma unroll
+        for (int j0 = 0; j0 < HC; j0 += BATCH) {
+          double cv[BATCH];
+#pragma unroll
+          for (int jj = 0; jj < BATCH; ++jj) {
+            const int col = n0 + cbase + j0 + jj;
+            cv[jj] = (reads_c && col < N) ? __ldcg(ep.C + row + (long long)col * ep.ldc) : 0.0;
+          }
+#pragma unroll
+          for (int jj = 0; jj < BATCH; ++jj) {
+            const int j = j0 + jj;
+            const int col = n0 + cbase + j;
+            if (col < N) {
+              const int k = ea + scB[vb.c0 + col] - 14;
+              const double dh = scaled_float_to_double(hi[j], k), dl = scaled_float_to_double(lo[j], k);
+              if (ep.mode == 0) {
+                double *p = ep.C + row + (long long)col * ep.ldc;
+                double x;
+                if (subtract) x = (cv[jj] - dh) - dl;
+                else if (plain) x = dh + dl;
+                else {
+                  const double val = dh + dl;
+                  x = (ep.beta == 0.0) ? ep.alpha * val : fma(ep.alpha, val, ep.beta * cv[jj]);
+                }
+                *p = x;
+                if (ep.out.base) {
+                  __nv_bfloat16 *o = ep.out.base + row + (long long)col * ep.out.ld;
+                  if (ep.out.scale) write_fixed_slices(x, ep.out.scale[col], o, ep.out.plane, ep.out.S);
+                  else write_slices(x, o, ep.out.plane, ep.out.S);
+                }
+              } else {
+                ep.Pd[(long long)z * M * N + row + (long long)col * M] = dh + dl;
+              }
+            }
           }
         }
       }
@@ -311,14 +382,17 @@ int launch_tcx(const CUtensorMap &ma, const CUtensorMap &mb, TcView va, TcView v
     attr_dev = dev;
   }
   long long tiles = (long long)ceil_div(M, TC_BM) * ceil_div(N, BN);
-  if (tiles > 0x7fffffffLL || splits > 65535) return PURL_ERR_UNSUPPORTED;
+  if (tiles * splits > 0x7fffffffLL) return PURL_ERR_UNSUPPORTED;
+  const DeviceInfo *di = device_info();
+  long long grid = tiles * splits;
+  if (grid > di->num_sms) grid = di->num_sms;  // persistent: one block per SM walks the work list
   double flops = 2.0 * M * (double)N * K;
   double bytes = (double)S * 2.0 * ((double)M * K + (double)N * K) +
                  (ep.mode == 0 ? 8.0 * M * N * (ep.beta != 0.0 ? 2 : 1) + (ep.out.base ? 2.0 * ep.out.S * M * N : 0)
                                : 8.0 * M * N * splits);
-  LaunchScope ls(KC_GEMM_TC, s, flops, bytes);
-  tcx_gemm_kernel<S, ALL, BN><<<dim3((unsigned)tiles, splits), TCX_THREADS, Cfg::SMEM, s>>>(
-      ma, mb, va, vb, M, N, K, k_chunk, scA, scB, ep, ctrl);
+  LaunchScope ls(KC_GEMM_TC, s, flops, bytes, ep.tag ? ep.tag : "tcx_gemm_kernel");
+  tcx_gemm_kernel<S, ALL, BN><<<(unsigned)grid, TCX_THREADS, Cfg::SMEM, s>>>(ma, mb, va, vb, M, N, K, k_chunk,
+                                                                             splits, scA, scB, ep, ctrl);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
@@ -330,7 +404,7 @@ int split_exact(int R, int Cc, const double *X, long long ldx, Slices dst, const
   if (Cc <= 0) return PURL_OK;
   if (!scale_from && !dst.scale) return PURL_ERR_UNSUPPORTED;
   int grid = Cc < di->num_sms * 32 ? Cc : di->num_sms * 32;
-  LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc);
+  LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc, "split_exact_kernel");
   split_exact_kernel<<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
@@ -340,7 +414,7 @@ int column_norm_exponents(int R, int Cc, const double *X, long long ldx, int *e,
   if (!di) return PURL_ERR_CUDA;
   if (Cc <= 0) return PURL_OK;
   int grid = Cc < di->num_sms * 32 ? Cc : di->num_sms * 32;
-  LaunchScope ls(KC_OTHER, s, 0.0, 8.0 * (double)R * Cc);
+  LaunchScope ls(KC_OTHER, s, 0.0, 8.0 * (double)R * Cc, "col_norm_exp_kernel");
   col_norm_exp_kernel<<<grid, 256, 0, s>>>(R, Cc, X, ldx, e);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }

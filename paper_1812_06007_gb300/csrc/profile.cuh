@@ -17,9 +17,10 @@ enum KernelClass {
 // Counts every kernel launch; when timing is on, brackets the launch with two
 // CUDA events on its stream and books `flops` / `bytes` to the class.
 struct LaunchScope {
-  LaunchScope(int cls, cudaStream_t s, double flops = 0.0, double bytes = 0.0);
+  LaunchScope(int cls, cudaStream_t s, double flops = 0.0, double bytes = 0.0, const char *name = nullptr);
   ~LaunchScope();
   int cls_;
+  const char *name_;
   cudaStream_t s_;
   double flops_, bytes_;
   cudaEvent_t e0_ = nullptr, e1_ = nullptr;

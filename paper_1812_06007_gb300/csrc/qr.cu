@@ -329,7 +329,7 @@ static int apply_block(int rows, int bw, int nc, double *C, int ldc, const doubl
   int splits, chunk;
   choose_splits(bw, nc, rows, di->num_sms, &splits, &chunk);
   PURL_TRY(gemm_f64_splitk(true, false, bw, nc, rows, splits, chunk, w.Vb, rows, C, ldc, w.Wp, s));
-  { LaunchScope ls(KC_OTHER, s);
+  { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "reduce_tmul_kernel");
   reduce_tmul_kernel<<<ceil_div(nc, 32), 256, 0, s>>>(bw, nc, splits, w.Wp, T, trans, w.W2); }
   PURL_CUDA_TRY(cudaGetLastError());
   return gemm_f64(false, false, rows, nc, bw, -1.0, w.Vb, rows, w.W2, bw, 1.0, C, ldc, s);
@@ -351,7 +351,7 @@ int panel_factor(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *
   long long ldf_ll = ldf, ldv_ll = ldv;
   void *args[] = {&rows, &bw, &ch, &Fp, &ldf_ll, &w.Vb, &ldv_ll, &taup, &w.part, &w.rowk, &counter,
                   (void *)&di->ctrl};
-  LaunchScope ls(KC_PANEL, s, 2.0 * rows * bw * (double)bw, 16.0 * rows * bw);
+  LaunchScope ls(KC_PANEL, s, 2.0 * rows * bw * (double)bw, 16.0 * rows * bw, "panel_kernel");
   PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel, dim3(P), dim3(PNT), args, smem, s));
   return PURL_OK;
 }
@@ -359,14 +359,14 @@ int panel_factor(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *
 // T factor of one panel from split-K partials of its Gram matrix V^T V.
 int larft_from_gram(int bw, int splits, const double *Gp, const double *taup, double *Tp, cudaStream_t s,
                     bool tau_from_gram) {
-  { LaunchScope ls(KC_OTHER, s); larft_kernel<<<1, 256, 0, s>>>(bw, splits, Gp, taup, Tp, tau_from_gram); }
+  { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "larft_kernel"); larft_kernel<<<1, 256, 0, s>>>(bw, splits, Gp, taup, Tp, tau_from_gram); }
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
 int extract_v(int rows, int bw, const double *Fp, int ldf, double *Vb, cudaStream_t s) {
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
-  { LaunchScope ls(KC_OTHER, s);
+  { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "extract_v_kernel");
     extract_v_kernel<<<grid_for((long long)rows * bw, di), 256, 0, s>>>(rows, bw, Fp, ldf, Vb, rows); }
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
@@ -374,7 +374,7 @@ int extract_v(int rows, int bw, const double *Fp, int ldf, double *Vb, cudaStrea
 int set_identity(int m, int n, double *Q, int ldq, cudaStream_t s) {
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
-  { LaunchScope ls(KC_OTHER, s); set_identity_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, Q, ldq); }
+  { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "set_identity_kernel"); set_identity_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, Q, ldq); }
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
@@ -427,7 +427,7 @@ int qr_sign_fix(int m, int n, const double *F, int ldf, double *Q, int ldq, doub
   if (!di) return PURL_ERR_CUDA;
   long long tot = (Q ? (long long)m * n : 0) + (R ? (long long)n * n : 0);
   if (tot == 0) return PURL_OK;
-  { LaunchScope ls(KC_OTHER, s); sign_fix_kernel<<<grid_for(tot, di), 256, 0, s>>>(m, n, F, ldf, Q, ldq, R, ldr); }
+  { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "sign_fix_kernel"); sign_fix_kernel<<<grid_for(tot, di), 256, 0, s>>>(m, n, F, ldf, Q, ldq, R, ldr); }
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
@@ -435,7 +435,7 @@ int copy_matrix(int m, int n, const double *X, int ldx, double *Y, int ldy, cuda
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
   if ((long long)m * n == 0) return PURL_OK;
-  { LaunchScope ls(KC_OTHER, s); copy_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, X, ldx, Y, ldy); }
+  { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "copy_kernel"); copy_kernel<<<grid_for((long long)m * n, di), 256, 0, s>>>(m, n, X, ldx, Y, ldy); }
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
@@ -443,7 +443,7 @@ int transpose_f64(int R, int Cc, const double *X, int ldx, double *Y, int ldy, c
   if ((long long)R * Cc == 0) return PURL_OK;
   dim3 grid(ceil_div(R, 32), ceil_div(Cc, 32));
   if (grid.y > 65535) return PURL_ERR_UNSUPPORTED;
-  { LaunchScope ls(KC_OTHER, s, 0.0, 16.0 * (double)R * Cc);
+  { LaunchScope ls(KC_OTHER, s, 0.0, 16.0 * (double)R * Cc, "transpose_kernel");
     transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(R, Cc, X, ldx, Y, ldy); }
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }

@@ -43,6 +43,7 @@ void choose_splits(int m, int n, int k, int num_sms, int *splits, int *k_chunk);
 namespace {
 
 constexpr int kChunkAlign = 256;  // exact-accumulation chunk of the tcx engine
+constexpr int kGramParts = 256;   // row chunks of the panel Gram matrix
 
 // Householder vectors with v_k = 1 satisfy |v_i| <= 1 (v = x / (x_0 - beta)
 // and |x_0 - beta| >= ||x||).  Each panel's V is rounded once to the grid
@@ -57,70 +58,94 @@ constexpr int kVExp = 1;
 // (the last digit of S slices at exponent kVExp), write V^ back over V, and
 // slice V^ naturally (exponent kVExp per column) and transposed (exponent of
 // each row's largest entry, <= kVExp, so the grid is carried exactly).
-__global__ void split_v_kernel(int rows, int bw, double *V, long long ldv, Slices vs, Slices vts) {
+__global__ void __launch_bounds__(256) split_v_kernel(int rows, int bw, double *V, long long ldv, Slices vs,
+                                                      Slices vts) {
+  __shared__ double q[32][QR_B + 1];
+  __shared__ int es[32];
   const int P = 7 + 8 * (vs.S - 1);
   const double unit = ldexp(1.0, kVExp - P);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
-    double q[QR_B];
-    unsigned long long mx = 0;
-#pragma unroll
-    for (int t = 0; t < QR_B; ++t) {
-      q[t] = 0.0;
-      if (t < bw) {
-        q[t] = (double)fixed_point(V[i + t * ldv], kVExp, P) * unit;
-        V[i + t * ldv] = q[t];
-        mx = max(mx, abs_bits(q[t]));
-      }
+  const int i0 = blockIdx.x * 32;
+  // round and write back, coalesced along rows (thread = (row, column group))
+  for (int e = threadIdx.x; e < 32 * QR_B; e += 256) {
+    const int ii = e & 31, t = e >> 5, i = i0 + ii;
+    double v = 0.0;
+    if (i < rows && t < bw) {
+      v = (double)fixed_point(V[i + t * ldv], kVExp, P) * unit;
+      V[i + t * ldv] = v;
     }
-    const int e = exp_above_bits(mx);
-    vts.scale[i] = e;
+    q[ii][t] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned long long mx = 0;
+    for (int t = 0; t < bw; ++t) mx = max(mx, abs_bits(q[threadIdx.x][t]));
+    es[threadIdx.x] = exp_above_bits(mx);
+    const int i = i0 + threadIdx.x;
+    if (i < rows) vts.scale[i] = es[threadIdx.x];
     if (i < bw) vs.scale[i] = kVExp;
-#pragma unroll
-    for (int t = 0; t < QR_B; ++t)
-      if (t < bw) {
-        write_fixed_slices(q[t], kVExp, vs.base + i + (long long)t * vs.ld, vs.plane, vs.S);
-        write_fixed_slices(q[t], e, vts.base + t + (long long)i * vts.ld, vts.plane, vts.S);
-      }
+  }
+  __syncthreads();
+  // natural slices: coalesced along rows
+  for (int e = threadIdx.x; e < 32 * QR_B; e += 256) {
+    const int ii = e & 31, t = e >> 5, i = i0 + ii;
+    if (i < rows && t < bw) write_fixed_slices(q[ii][t], kVExp, vs.base + i + (long long)t * vs.ld, vs.plane, vs.S);
+  }
+  // transposed slices: coalesced along columns
+  for (int e = threadIdx.x; e < 32 * QR_B; e += 256) {
+    const int t = e & 31, ii = e >> 5, i = i0 + ii;
+    if (i < rows && t < bw) write_fixed_slices(q[ii][t], es[ii], vts.base + t + (long long)i * vts.ld, vts.plane, vts.S);
   }
 }
 
 // W2(:, c) = op(T) * sum_z Pd_z(c, :)^T for each trailing column c, then the
-// slices of W2(:, c) with its own exponent.  One thread per column.
-__global__ void __launch_bounds__(128) reduce_tmul_slices_kernel(int bw, int nc, int splits,
+// slices of W2(:, c) with its own exponent.  Block = 32 columns x 8 row groups
+// (thread (cx, ry) owns rows ry, ry+8, ry+16, ry+24 of column cx).
+__global__ void __launch_bounds__(256) reduce_tmul_slices_kernel(int bw, int nc, int splits,
                                                                  const double *__restrict__ Pd,
                                                                  const double *__restrict__ T, bool trans,
                                                                  Slices W2s) {
   __shared__ double Ts[QR_B][QR_B + 1];
+  __shared__ double ws[QR_B][33];
+  __shared__ unsigned long long mxs[8][32];
+  const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + cx;
   for (int e = threadIdx.x; e < QR_B * QR_B; e += blockDim.x) {
-    int i = e % QR_B, j = e / QR_B;
+    const int i = e % QR_B, j = e / QR_B;
     Ts[i][j] = trans ? T[j + i * QR_B] : T[e];  // Ts = op(T)
   }
-  __syncthreads();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
-  double w[QR_B];
 #pragma unroll
-  for (int l = 0; l < QR_B; ++l) {
-    double s = 0.0;
-    if (l < bw)
-      for (int z = 0; z < splits; ++z) s += Pd[(long long)z * nc * bw + c + (long long)l * nc];
-    w[l] = s;
+  for (int q = 0; q < 4; ++q) {
+    const int l = ry + 8 * q;
+    double v = 0.0;
+    if (c < nc && l < bw)
+      for (int z = 0; z < splits; ++z) v += Pd[(long long)z * nc * bw + c + (long long)l * nc];
+    ws[l][cx] = v;
   }
-  double w2[QR_B];
+  __syncthreads();
+  double w2[4];
   unsigned long long mx = 0;
 #pragma unroll
-  for (int r = 0; r < QR_B; ++r) {
+  for (int q = 0; q < 4; ++q) {
+    const int r = ry + 8 * q;
     double t = 0.0;
-#pragma unroll
-    for (int l = 0; l < QR_B; ++l) t = fma(Ts[r][l], w[l], t);
-    w2[r] = t;
+#pragma unroll 8
+    for (int l = 0; l < QR_B; ++l) t = fma(Ts[r][l], ws[l][cx], t);
+    w2[q] = t;
     if (r < bw) mx = max(mx, abs_bits(t));
   }
-  const int e = exp_above_bits(mx);
-  W2s.scale[c] = e;
+  mxs[ry][cx] = mx;
+  __syncthreads();
+  unsigned long long m = 0;
 #pragma unroll
-  for (int r = 0; r < QR_B; ++r)
-    if (r < bw) write_fixed_slices(w2[r], e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
+  for (int y = 0; y < 8; ++y) m = max(m, mxs[y][cx]);
+  const int e = exp_above_bits(m);
+  if (c >= nc) return;
+  if (ry == 0) W2s.scale[c] = e;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = ry + 8 * q;
+    if (r < bw) write_fixed_slices(w2[q], e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
+  }
 }
 
 // Explicit rounded V of an outer block: column t (0 <= t < nbw) of the block
@@ -141,34 +166,64 @@ __global__ void extract_round_v_kernel(int rows, int nbw, const double *__restri
 }
 
 // Slices of X^T (nbw x rows) with one exponent per row of X (rows x nbw):
-// one thread per row, two passes over the row (maximum, then digits).
-__global__ void split_rows_t_kernel(int rows, int nbw, const double *__restrict__ X, long long ldx, Slices dst) {
+// row_exp_kernel takes the exponent of each row's maximum (coalesced across
+// rows), split_rows_t_kernel writes the digits through a 32 x 32 shared tile
+// so both the reads of X and the writes of X^T's slices are coalesced.
+__global__ void row_exp_kernel(int rows, int nbw, const double *__restrict__ X, long long ldx, int *e_out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
     unsigned long long mx = 0;
     for (int t = 0; t < nbw; ++t) mx = max(mx, abs_bits(X[i + (long long)t * ldx]));
-    const int e = exp_above_bits(mx);
-    dst.scale[i] = e;
-    for (int t = 0; t < nbw; ++t)
-      write_fixed_slices(X[i + (long long)t * ldx], e, dst.base + t + (long long)i * dst.ld, dst.plane, dst.S);
+    e_out[i] = exp_above_bits(mx);
   }
 }
 
-// W2(:, c) = sum_z Pd_z(c, :)^T (nbw entries), sliced with its own exponent.
-__global__ void reduce_slices_kernel(int nbw, int nc, int splits, const double *__restrict__ Pd, Slices W2s) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
-  unsigned long long mx = 0;
-  for (int r = 0; r < nbw; ++r) {
-    double v = 0.0;
-    for (int z = 0; z < splits; ++z) v += Pd[(long long)z * nc * nbw + c + (long long)r * nc];
-    mx = max(mx, abs_bits(v));
+__global__ void split_rows_t_kernel(int rows, int nbw, const double *__restrict__ X, long long ldx, Slices dst) {
+  __shared__ double tile[32][33];
+  const int i0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int i = i0 + threadIdx.x, t = t0 + j;
+    tile[j][threadIdx.x] = (i < rows && t < nbw) ? X[i + (long long)t * ldx] : 0.0;
   }
-  const int e = exp_above_bits(mx);
-  W2s.scale[c] = e;
-  for (int r = 0; r < nbw; ++r) {
-    double v = 0.0;
-    for (int z = 0; z < splits; ++z) v += Pd[(long long)z * nc * nbw + c + (long long)r * nc];
-    write_fixed_slices(v, e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int t = t0 + threadIdx.x, i = i0 + j;  // dst(t, i) = X(i, t)
+    if (i < rows && t < nbw)
+      write_fixed_slices(tile[threadIdx.x][j], dst.scale[i], dst.base + t + (long long)i * dst.ld, dst.plane, dst.S);
+  }
+}
+
+// W2(:, c) = sum_z Pd_z(c, :)^T (nbw <= QR_NB entries), sliced with its own
+// exponent.  Block = 32 columns x 8 row groups; thread (cx, ry) owns rows
+// ry, ry + 8, ... of column cx.
+__global__ void __launch_bounds__(256) reduce_slices_kernel(int nbw, int nc, int splits, const double *__restrict__ Pd,
+                                                            Slices W2s) {
+  constexpr int RPT = QR_NB / 8;
+  __shared__ unsigned long long mxs[8][32];
+  const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + cx;
+  double v[RPT];
+  unsigned long long mx = 0;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = ry + 8 * q;
+    double a = 0.0;
+    if (c < nc && r < nbw)
+      for (int z = 0; z < splits; ++z) a += Pd[(long long)z * nc * nbw + c + (long long)r * nc];
+    v[q] = a;
+    mx = max(mx, abs_bits(a));
+  }
+  mxs[ry][cx] = mx;
+  __syncthreads();
+  unsigned long long m = 0;
+#pragma unroll
+  for (int y = 0; y < 8; ++y) m = max(m, mxs[y][cx]);
+  const int e = exp_above_bits(m);
+  if (c >= nc) return;
+  if (ry == 0) W2s.scale[c] = e;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = ry + 8 * q;
+    if (r < nbw) write_fixed_slices(v[q], e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
   }
 }
 
@@ -178,6 +233,57 @@ __global__ void sum_partials_kernel(int count, int splits, const double *__restr
     double v = 0.0;
     for (int z = 0; z < splits; ++z) v += P[(long long)z * count + e];
     out[e] = v;
+  }
+}
+
+// Y = G(0:kb, kb:kb+bw) T_k  (kb x bw, ld kb).  Thread (i, j) per entry.
+__global__ void tout_y_kernel(int kb, int bw, const double *__restrict__ G, int ldg, const double *__restrict__ Tk,
+                              double *Y) {
+  const int i = blockIdx.x, j = threadIdx.x;
+  if (i >= kb || j >= bw) return;
+  double acc = 0.0;
+  for (int t = 0; t <= j; ++t) acc = fma(G[i + (long long)(kb + t) * ldg], Tk[t + j * QR_B], acc);  // T_k upper
+  Y[i + (long long)j * kb] = acc;
+}
+
+// T_out(0:kb, kb:kb+bw) = -T_out(0:kb, 0:kb) Y, T_out upper triangular.
+__global__ void tout_block_kernel(int kb, int bw, const double *__restrict__ Y, double *Tout, int ldt) {
+  const int i = blockIdx.x, j = threadIdx.x;
+  if (i >= kb || j >= bw) return;
+  double acc = 0.0;
+  for (int l = i; l < kb; ++l) acc = fma(Tout[i + (long long)l * ldt], Y[l + (long long)j * kb], acc);
+  Tout[i + (long long)(kb + j) * ldt] = -acc;
+}
+
+// FP64 Gram matrix partials of the rounded panel V (rows x bw): block z
+// covers rows [z*chunk, (z+1)*chunk) and writes its bw x bw partial at
+// Gp + z*bw*bw (the layout larft_from_gram sums).
+__global__ void __launch_bounds__(256) gram_kernel(int rows, int bw, int chunk, const double *__restrict__ V, int ldv,
+                                                   double *Gp) {
+  __shared__ double Vs[64][QR_B + 1];
+  const int r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int e0 = threadIdx.x;  // outputs e0, e0 + 256, e0 + 512, e0 + 768 of the 32 x 32
+  for (int rb = r0; rb < r1; rb += 64) {
+    const int nrow = min(64, r1 - rb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * QR_B; e += 256) {
+      const int i = e % 64, t = e / 64;
+      Vs[i][t] = (i < nrow && t < bw) ? V[(rb + i) + (long long)t * ldv] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + q * 256, a = e % QR_B, b = e / QR_B;
+      double s = acc[q];
+      for (int i = 0; i < nrow; ++i) s = fma(Vs[i][a], Vs[i][b], s);
+      acc[q] = s;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = e0 + q * 256, a = e % QR_B, b = e / QR_B;
+    if (a < bw && b < bw) Gp[(long long)blockIdx.x * bw * bw + a + b * bw] = acc[q];
   }
 }
 
@@ -199,10 +305,9 @@ void splits_for(int M, int N, int K, int num_sms, int *splits, int *chunk) {
 // Slices of the panel's V (natural and transposed) from w.base.Vb (rows x bw).
 int slice_panel(int rows, int bw, QrMixWork &w, cudaStream_t s) {
   const DeviceInfo *di = device_info();
-  int grid = ceil_div(rows, 256);
-  if (grid > di->num_sms * 8) grid = di->num_sms * 8;
-  { LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 4.0 * w.S) * (double)rows * bw);
-    split_v_kernel<<<grid, 256, 0, s>>>(rows, bw, w.base.Vb, rows, w.Vs, w.Vts); }
+  (void)di;
+  { LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 4.0 * w.S) * (double)rows * bw, "split_v_kernel");
+    split_v_kernel<<<ceil_div(rows, 32), 256, 0, s>>>(rows, bw, w.base.Vb, rows, w.Vs, w.Vts); }
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
@@ -224,10 +329,11 @@ int apply_block_mixed(int rows, int bw, int nc, double *Cp, int ldc, const Slice
   TcEpilogue ep;
   ep.mode = 2;
   ep.Pd = w.Pd;
+  ep.tag = "tcx inner V^T C";
   PURL_TRY(tcx_gemm_view(Cs, r0, c0, w.Vs, 0, 0, nc, bw, rows, w.S, ep, sp, ch, s));
   // W2 = op(T) W, sliced
-  { LaunchScope ls(KC_OTHER, s, 2.0 * bw * bw * (double)nc, 8.0 * sp * (double)nc * bw);
-    reduce_tmul_slices_kernel<<<ceil_div(nc, 128), 128, 0, s>>>(bw, nc, sp, w.Pd, T, trans, w.W2s); }
+  { LaunchScope ls(KC_OTHER, s, 2.0 * bw * bw * (double)nc, 8.0 * sp * (double)nc * bw, "reduce_tmul_slices_kernel");
+    reduce_tmul_slices_kernel<<<ceil_div(nc, 32), 256, 0, s>>>(bw, nc, sp, w.Pd, T, trans, w.W2s); }
   PURL_CUDA_TRY(cudaGetLastError());
   // C <- C - V W2 (FP64)
   TcEpilogue up;
@@ -236,6 +342,7 @@ int apply_block_mixed(int rows, int bw, int nc, double *Cp, int ldc, const Slice
   up.beta = 1.0;
   up.C = Cp;
   up.ldc = ldc;
+  up.tag = "tcx inner update";
   return tcx_gemm_view(w.Vts, 0, 0, w.W2s, 0, 0, rows, nc, bw, w.S, up, 1, kChunkAlign, s);
 }
 
@@ -254,12 +361,15 @@ int outer_prepare(int rows, int nbw, const double *FJ, int ldf, int m, int first
                   QrMixWork &w, cudaStream_t s) {
   const DeviceInfo *di = device_info();
   const int P = 7 + 8 * (w.S - 1);
-  { LaunchScope ls(KC_OTHER, s, 0.0, 16.0 * rows * (double)nbw);
+  { LaunchScope ls(KC_OTHER, s, 0.0, 16.0 * rows * (double)nbw, "extract_round_v_kernel");
     extract_round_v_kernel<<<launch_grid((long long)rows * nbw, di->num_sms * 16), 256, 0, s>>>(rows, nbw, FJ, ldf,
                                                                                                    w.Vo, m, P); }
   PURL_CUDA_TRY(cudaGetLastError());
-  { LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * w.S) * rows * (double)nbw);
-    split_rows_t_kernel<<<launch_grid(rows, di->num_sms * 8), 256, 0, s>>>(rows, nbw, w.Vo, m, w.Vots); }
+  { LaunchScope ls(KC_SPLIT, s, 0.0, 8.0 * rows * (double)nbw, "row_exp_kernel");
+    row_exp_kernel<<<launch_grid(rows, di->num_sms * 8), 256, 0, s>>>(rows, nbw, w.Vo, m, w.Vots.scale); }
+  { LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * w.S) * rows * (double)nbw, "split_rows_t_kernel");
+    split_rows_t_kernel<<<dim3(ceil_div(rows, 32), ceil_div(nbw, 32)), dim3(32, 8), 0, s>>>(rows, nbw, w.Vo, m,
+                                                                                           w.Vots); }
   PURL_CUDA_TRY(cudaGetLastError());
   if (!build_t) return PURL_OK;
   PURL_TRY(split_exact(rows, nbw, w.Vo, m, w.Vos, nullptr, s));
@@ -269,8 +379,9 @@ int outer_prepare(int rows, int nbw, const double *FJ, int ldf, int m, int first
   TcEpilogue g;
   g.mode = 2;
   g.Pd = w.Go;
+  g.tag = "tcx outer Gram (all pairs)";
   PURL_TRY(tcx_gemm_all_pairs(w.Vos, 0, 0, w.Vos, 0, 0, nbw, nbw, rows, w.S, g, gs, gch, s));
-  { LaunchScope ls(KC_OTHER, s);
+  { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "sum_partials_kernel");
     sum_partials_kernel<<<launch_grid((long long)nbw * nbw, 256), 256, 0, s>>>(nbw * nbw, gs, w.Go, w.Tt); }
   PURL_CUDA_TRY(cudaGetLastError());
   double *G = w.Tt;  // nbw x nbw, ld nbw
@@ -279,12 +390,15 @@ int outer_prepare(int rows, int nbw, const double *FJ, int ldf, int m, int first
   for (int kb = 0, k = 0; kb < nbw; kb += QR_B, ++k) {
     const int bw = min(QR_B, nbw - kb);
     const double *Tk = w.base.T + (size_t)(first_panel + k) * QR_B * QR_B;
-    { LaunchScope ls(KC_OTHER, s); place_tk_kernel<<<1, 256, 0, s>>>(QR_NB, kb, bw, Tk, Tout); }
+    { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "place_tk_kernel"); place_tk_kernel<<<1, 256, 0, s>>>(QR_NB, kb, bw, Tk, Tout); }
     PURL_CUDA_TRY(cudaGetLastError());
     if (kb == 0) continue;
-    // X = T_out(0:kb, 0:kb) G(0:kb, kb:kb+bw);  T_out(0:kb, kb:kb+bw) = -X T_k
-    PURL_TRY(gemm_f64(false, false, kb, bw, kb, 1.0, Tout, QR_NB, G + (size_t)kb * nbw, nbw, 0.0, X, kb, s));
-    PURL_TRY(gemm_f64(false, false, kb, bw, bw, -1.0, X, kb, Tk, QR_B, 0.0, Tout + (size_t)kb * QR_NB, QR_NB, s));
+    // Y = G(0:kb, kb:kb+bw) T_k;  T_out(0:kb, kb:kb+bw) = -T_out(0:kb, 0:kb) Y
+    { LaunchScope ls(KC_OTHER, s, 2.0 * kb * bw * bw, 0.0, "tout_y_kernel");
+      tout_y_kernel<<<kb, QR_B, 0, s>>>(kb, bw, G, nbw, Tk, X); }
+    { LaunchScope ls(KC_OTHER, s, 1.0 * kb * kb * bw, 0.0, "tout_block_kernel");
+      tout_block_kernel<<<kb, QR_B, 0, s>>>(kb, bw, X, Tout, QR_NB); }
+    PURL_CUDA_TRY(cudaGetLastError());
   }
   return PURL_OK;
 }
@@ -306,6 +420,7 @@ int outer_apply(int rows, int nbw, int nc, double *Cp, int ldc, const Slices &Cs
   vt.mode = 0;
   vt.C = w.Vtl;
   vt.ldc = m;
+  vt.tag = "tcx outer V~ = V T";
   PURL_TRY(tcx_gemm_view(w.Vots, 0, 0, w.Ts, 0, 0, rows, nbw, nbw, w.S, vt, 1, kChunkAlign, s));
   PURL_TRY(split_exact(rows, nbw, w.Vtl, m, w.Vtls, nullptr, s));
   // re-slice the active block with fresh per-column exponents
@@ -323,9 +438,10 @@ int outer_apply(int rows, int nbw, int nc, double *Cp, int ldc, const Slices &Cs
   TcEpilogue ep;
   ep.mode = 2;
   ep.Pd = w.Pdo;
+  ep.tag = "tcx outer C^T V~";
   PURL_TRY(tcx_gemm_view(Cs, r0, c0, w.Vtls, 0, 0, nc, nbw, rows, w.S, ep, sp, ch, s));
-  { LaunchScope ls(KC_SPLIT, s, 0.0, 8.0 * sp * (double)nc * nbw);
-    reduce_slices_kernel<<<ceil_div(nc, 128), 128, 0, s>>>(nbw, nc, sp, w.Pdo, w.W2o); }
+  { LaunchScope ls(KC_SPLIT, s, 0.0, 8.0 * sp * (double)nc * nbw, "reduce_slices_kernel");
+    reduce_slices_kernel<<<ceil_div(nc, 32), 256, 0, s>>>(nbw, nc, sp, w.Pdo, w.W2o); }
   PURL_CUDA_TRY(cudaGetLastError());
   // C <- C - V W2
   TcEpilogue up;
@@ -334,6 +450,7 @@ int outer_apply(int rows, int nbw, int nc, double *Cp, int ldc, const Slices &Cs
   up.beta = 1.0;
   up.C = Cp;
   up.ldc = ldc;
+  up.tag = "tcx outer update";
   return tcx_gemm_view(w.Vots, 0, 0, w.W2o, 0, 0, rows, nc, nbw, w.S, up, 1, ceil_div(nbw, kChunkAlign) * kChunkAlign, s);
 }
 
@@ -357,6 +474,7 @@ int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w) {
   w->W2s.scale = ar.take<int>(nn);
   const size_t nout = (size_t)ceil_div(n > 0 ? n : 1, QR_NB);
   w->Tout = ar.take<double>(nout * QR_NB * QR_NB);
+  w->Gparts = ar.take<double>((size_t)kGramParts * QR_B * QR_B);
   w->Vo = ar.take<double>(mm * QR_NB);
   w->Vtl = ar.take<double>(mm * QR_NB);
   w->Go = ar.take<double>((size_t)QR_MAX_SPLITS * QR_NB * QR_NB);
@@ -392,11 +510,16 @@ int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t
       PURL_TRY(panel_factor(rj, bw, Fp, ldf, taup, w.base.counters + p, w.base, s));
       PURL_TRY(slice_panel(rj, bw, w, s));
       // T_k from the FP64 Gram matrix of the rounded V^ (exact to FP64 rounding)
-      int gs, gch;
-      choose_splits(bw, bw, rj, di->num_sms, &gs, &gch);
-      PURL_TRY(gemm_f64_splitk(true, false, bw, bw, rj, gs, gch, w.base.Vb, rj, w.base.Vb, rj, w.base.Gp, s));
+      int gchunk = ceil_div(ceil_div(rj, kGramParts), 64) * 64;
+      if (gchunk < 64) gchunk = 64;
+      const int gs = ceil_div(rj, gchunk);
+      { LaunchScope ls(KC_GEMM_F64, s, 2.0 * rj * bw * (double)bw, 8.0 * rj * bw, "gram_kernel");
+        gram_kernel<<<gs, 256, 0, s>>>(rj, bw, gchunk, w.base.Vb, rj, w.Gparts); }
+      { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "sum_partials_kernel");
+        sum_partials_kernel<<<ceil_div(bw * bw, 64), 64, 0, s>>>(bw * bw, gs, w.Gparts, w.base.Gp); }
+      PURL_CUDA_TRY(cudaGetLastError());
       double *Tp = w.base.T + (size_t)p * QR_B * QR_B;
-      PURL_TRY(larft_from_gram(bw, gs, w.base.Gp, taup, Tp, s, true));
+      PURL_TRY(larft_from_gram(bw, 1, w.base.Gp, taup, Tp, s, true));
       PURL_TRY(apply_block_mixed(rj, bw, nc_in, Fp + (size_t)bw * ldf, ldf, w.Fs, j0, j0 + bw, w.col_exp, Tp, true,
                                  w, s));
     }

@@ -24,6 +24,7 @@ struct QrMixWork {
   double *Vtl = nullptr;   // V~ = V op(T_out) (m x QR_NB, ld m)
   double *Go = nullptr;    // split-K partials of V^T V (QR_MAX_SPLITS x QR_NB x QR_NB)
   double *Tt = nullptr;    // scratch QR_NB x QR_NB (T_out^T, T-builder products)
+  double *Gparts = nullptr;  // row-chunk partials of a panel's FP64 Gram matrix
   double *Pdo = nullptr;   // split-K partials of W^T (kOuterSplits x n x QR_NB)
   Slices Vos;        // slices of V (rows x QR_NB)
   Slices Vots;       // slices of V^T (QR_NB x rows), scale per row of V

@@ -66,7 +66,7 @@ int launch_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, doubl
   long long nblk = (count + 3) / 4;
   long long want = (nblk + 255) / 256;
   int grid = (int)(want < (long long)di->num_sms * 8 ? want : (long long)di->num_sms * 8);
-  LaunchScope ls(KC_OTHER, stream, 0.0, 8.0 * count);
+  LaunchScope ls(KC_OTHER, stream, 0.0, 8.0 * count, "gaussian_kernel");
   gaussian_kernel<<<grid, 256, 0, stream>>>(seed, stream_id, rows, count, G, ldg);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }

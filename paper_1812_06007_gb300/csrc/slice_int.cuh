@@ -69,4 +69,18 @@ __device__ __forceinline__ void write_fixed_slices(double x, int e, __nv_bfloat1
   for (int s = 0; s < S; ++s) out[s * plane] = digit[s];
 }
 
+// The FP64 value of f * 2^k for a finite FP32 f, assembled from the bits of f
+// with integer operations (no FP64-pipe instruction).  Zero and FP32
+// subnormals (|f| < 2^-126, far below every value these kernels produce)
+// give zero.
+__device__ __forceinline__ double scaled_float_to_double(float f, int k) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e8 = (b >> 23) & 0xFFu;
+  if (e8 == 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const unsigned long long e11 = (unsigned long long)(int)(e8 + 896 + k);
+  const unsigned long long m = (unsigned long long)(b & 0x7FFFFFu) << 29;
+  return __longlong_as_double((long long)(sign | (e11 << 52) | m));
+}
+
 }  // namespace purl

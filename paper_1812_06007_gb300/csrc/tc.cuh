@@ -52,6 +52,7 @@ struct TcEpilogue {
   float *P = nullptr;
   double *Pd = nullptr;  // mode 2: FP64 partials
   Slices out;  // optional
+  const char *tag = nullptr;  // host-side name for the launch profiler
 };
 
 // Exact-accumulation slices (Ozaki-style splitting): every column c of X
