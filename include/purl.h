@@ -175,8 +175,9 @@ int purl_device_status(cudaStream_t stream);
 unsigned long long purl_launch_count(void);
 
 /* Opt-in timing: while enabled, every kernel launch is bracketed by two CUDA
- * events recorded on the stream it runs on, and its device time, algorithmic
- * flops and algorithmic bytes are booked to its class:
+ * events recorded on the stream it runs on, and its device time, flops and
+ * algorithmic bytes are booked to its class (for the tensor-core classes the
+ * flops are those issued: 2 m n k per slice pair multiplied):
  *   0 gemm_f64 (FP64 DFMA products), 1 panel_qr (Householder panels),
  *   2 gemm_tc (BF16 tensor-core products), 3 split (FP64 -> BF16 slicing),
  *   4 other (RNG, T factors, reductions, copies, sign fixes).
@@ -187,7 +188,8 @@ void purl_profile_reset(void);
 int purl_profile_read(int cls, long long *launches, double *ms, double *flops, double *bytes);
 const char *purl_profile_class_name(int cls);
 /* The same totals per kernel name (index 0, 1, ... until -1 is returned). */
-int purl_profile_read_named(int index, char *name, int name_len, long long *launches, double *ms);
+int purl_profile_read_named(int index, char *name, int name_len, long long *launches, double *ms,
+                            double *flops, double *bytes);
 
 #ifdef __cplusplus
 }

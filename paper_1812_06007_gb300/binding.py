@@ -50,7 +50,7 @@ SIGNATURES = {
                                ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "purl_profile_class_name": (ctypes.c_char_p, [_i]),
     "purl_profile_read_named": (_i, [_i, ctypes.c_char_p, _i, ctypes.POINTER(ctypes.c_longlong),
-                                     ctypes.POINTER(_d)]),
+                                     ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
 }
 
 _lock = threading.Lock()
@@ -273,9 +273,10 @@ def purl_profile_read_named() -> dict:
     while True:
         buf = ctypes.create_string_buffer(128)
         n = ctypes.c_longlong(0)
-        ms = ctypes.c_double(0)
-        if lib().purl_profile_read_named(i, buf, 128, ctypes.byref(n), ctypes.byref(ms)) != 0:
+        ms, fl, by = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        if lib().purl_profile_read_named(i, buf, 128, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                         ctypes.byref(by)) != 0:
             break
-        out[buf.value.decode()] = {"launches": n.value, "ms": ms.value}
+        out[buf.value.decode()] = {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
         i += 1
     return out

@@ -238,8 +238,8 @@ int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcView va, TcView vb
   long long tiles = (long long)ceil_div(M, TC_BM) * ceil_div(N, BN);
   if (tiles > 0x7fffffffLL || splits > 65535) return PURL_ERR_UNSUPPORTED;
   dim3 grid((unsigned)tiles, splits);
-  int prods = S * (S + 1) / 2;
-  double flops = 2.0 * M * (double)N * K;  // algorithmic: one product, not one per slice pair
+  const int prods = S * (S + 1) / 2;
+  double flops = 2.0 * M * (double)N * K * prods;  // issued tensor-core work: one product per slice pair
   double bytes = (double)S * 2.0 * ((double)M * K + (double)N * K) +
                  (ep.mode == 0 ? 8.0 * M * N * (ep.beta != 0.0 ? 2 : 1) + (ep.out.base ? 2.0 * ep.out.S * M * N : 0)
                                : 4.0 * M * N * splits);

@@ -386,7 +386,9 @@ int launch_tcx(const CUtensorMap &ma, const CUtensorMap &mb, TcView va, TcView v
   const DeviceInfo *di = device_info();
   long long grid = tiles * splits;
   if (grid > di->num_sms) grid = di->num_sms;  // persistent: one block per SM walks the work list
-  double flops = 2.0 * M * (double)N * K;
+  // issued tensor-core work: every slice pair is one BF16 product
+  const int pairs = ALL ? S * S : S * (S + 1) / 2;
+  double flops = 2.0 * M * (double)N * K * pairs;
   double bytes = (double)S * 2.0 * ((double)M * K + (double)N * K) +
                  (ep.mode == 0 ? 8.0 * M * N * (ep.beta != 0.0 ? 2 : 1) + (ep.out.base ? 2.0 * ep.out.S * M * N : 0)
                                : 8.0 * M * N * splits);

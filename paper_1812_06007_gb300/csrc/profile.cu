@@ -124,7 +124,8 @@ int purl_profile_read(int cls, long long *launches, double *ms, double *flops, d
   return PURL_OK;
 }
 
-int purl_profile_read_named(int index, char *name, int name_len, long long *launches, double *ms) {
+int purl_profile_read_named(int index, char *name, int name_len, long long *launches, double *ms, double *flops,
+                            double *bytes) {
   std::lock_guard<std::mutex> lock(g_mu);
   drain_locked();
   if (index < 0 || index >= (int)g_named.size()) return -1;
@@ -135,6 +136,8 @@ int purl_profile_read_named(int index, char *name, int name_len, long long *laun
   }
   if (launches) *launches = it->second.launches;
   if (ms) *ms = it->second.ms;
+  if (flops) *flops = it->second.flops;
+  if (bytes) *bytes = it->second.bytes;
   return PURL_OK;
 }
 
