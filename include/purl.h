@@ -151,6 +151,34 @@ int purl_gemm_tc(char transa, char transb, int m, int n, int k, double alpha, co
                  int exact, cudaStream_t stream);
 
 /*
+ * purl_gemm_tc_noalloc -- purl_gemm_tc (exact = 0) that allocates no device
+ * memory.  (Library plumbing: the paper has no counterpart.)
+ *
+ * For callers that cannot call cudaMalloc or cudaMallocAsync at the point of
+ * the call: code that runs after a framework has handed all device memory to
+ * its own caching allocator, real-time loops that forbid allocation (its
+ * latency and the risk of failing mid-run), or hosts that budget device
+ * memory up front.  The operand slices are staged in a file-scope device
+ * array of 24 MiB that every GPU which loads libpurl holds until the process
+ * exits; nothing is allocated or freed per call (no cudaMalloc, cudaFree or
+ * allocating library routine).
+ *   - Size limit: the BF16 slices of both operands, 2 * slices * (64-rounded
+ *     k) * (m + n) bytes plus alignment, must fit in the 24 MiB; larger
+ *     requests return PURL_ERR_NOMEM without doing any work.
+ *   - The first call on a device sets the array up (resolves its device
+ *     address with cudaGetSymbolAddress and clears a status word, which
+ *     synchronises the device); make that first call before any stream
+ *     capture on that device.
+ *   - Every call reuses the same array, which keeps the last call's
+ *     contents.  Calls that overlap on the GPU (different streams, or host
+ *     threads racing) race on it: serialise them, e.g. on one stream.
+ * Arguments, results and return codes are those of purl_gemm_tc with exact = 0.
+ */
+int purl_gemm_tc_noalloc(char transa, char transb, int m, int n, int k, double alpha, const double *A,
+                         int lda, const double *B, int ldb, double beta, double *C, int ldc, int slices,
+                         cudaStream_t stream);
+
+/*
  * purl_urv_truncate -- rank-k approximation of Section 5:
  *   A_k = U(:,1:k) R(1:k,:) V^T   (m x n, written to Ak, ldak >= m), 0 <= k <= n.
  * purl_urv_reconstruct is the k = n case (U R V^T).

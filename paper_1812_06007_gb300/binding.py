@@ -40,6 +40,7 @@ SIGNATURES = {
     "purl_qr_workspace_bytes": (_sz, [_i, _i, _i]),
     "purl_gemm_f64": (_i, [_c, _c, _i, _i, _i, _d, _p, _i, _p, _i, _d, _p, _i, _p]),
     "purl_gemm_tc": (_i, [_c, _c, _i, _i, _i, _d, _p, _i, _p, _i, _d, _p, _i, _i, _i, _p]),
+    "purl_gemm_tc_noalloc": (_i, [_c, _c, _i, _i, _i, _d, _p, _i, _p, _i, _d, _p, _i, _i, _p]),
     "purl_urv_truncate": (_i, [_i, _i, _i, _p, _i, _p, _i, _p, _i, _p, _i, _p]),
     "purl_urv_reconstruct": (_i, [_i, _i, _p, _i, _p, _i, _p, _i, _p, _i, _p]),
     "purl_device_status": (_i, [_p]),
@@ -213,6 +214,24 @@ def purl_gemm_tc(transa: str, transb: str, A, B, alpha: float = 1.0, beta: float
     st = lib().purl_gemm_tc(transa.encode(), transb.encode(), m, n, k, alpha, _ptr(A), _ld(A), _ptr(B),
                             _ld(B), beta, _ptr(C), _ld(C), slices, int(bool(exact)), _stream(stream))
     _check("purl_gemm_tc", st)
+    return C
+
+
+def purl_gemm_tc_noalloc(transa: str, transb: str, A, B, alpha: float = 1.0, beta: float = 0.0, C=None,
+                         slices: int = 3, stream=None):
+    """purl_gemm_tc (floating slices) staged in the library's static device scratch: allocates nothing."""
+    _cuda_check(A, B)
+    m = A.shape[0] if transa == "N" else A.shape[1]
+    k = A.shape[1] if transa == "N" else A.shape[0]
+    n = B.shape[1] if transb == "N" else B.shape[0]
+    if C is None:
+        C = empty_colmajor(m, n, A.device)
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs C")
+    _cuda_check(C)
+    st = lib().purl_gemm_tc_noalloc(transa.encode(), transb.encode(), m, n, k, alpha, _ptr(A), _ld(A), _ptr(B),
+                                    _ld(B), beta, _ptr(C), _ld(C), slices, _stream(stream))
+    _check("purl_gemm_tc_noalloc", st)
     return C
 
 

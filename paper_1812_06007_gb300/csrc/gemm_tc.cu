@@ -349,4 +349,148 @@ int tc_gemm(const Slices &A, const Slices &B, int M, int N, int K, int S, const 
   return tc_gemm_view(A, 0, 0, B, 0, 0, M, N, K, S, ep, splits, k_chunk, s);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of purl_gemm_tc.  Its operand slices (and the
+// status word its bounded waits report to) live in one file-scope device
+// array instead of memory from cudaMalloc/cudaMallocAsync, so it can be used
+// by callers that must not allocate device memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)24 << 20;  // 24 MiB on every device that loads the library
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch on this device
+};
+
+__global__ void noalloc_scale_kernel(int m, int n, double beta, double *C, long long ldc) {
+  long long total = (long long)m * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e % m), j = (int)(e / m);
+    double *p = C + i + j * ldc;
+    *p = (beta == 0.0) ? 0.0 : beta * *p;
+  }
+}
+
+// Once per device, with that device current: resolve the array's device
+// address (the host-side symbol is not a device pointer) and clear the
+// status word kept at its start.
+int noalloc_setup(NoAllocDevice **out) {
+  static std::mutex mu;
+  static NoAllocDevice devs[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PURL_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  NoAllocDevice &d = devs[dev];
+  if (!d.ready) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return PURL_ERR_CUDA;
+    if (cudaMemset(ptr, 0, sizeof(DeviceControl)) != cudaSuccess) return PURL_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return PURL_ERR_CUDA;
+    d.scratch = static_cast<unsigned char *>(ptr);
+    d.ready = true;
+  }
+  *out = &d;
+  return PURL_OK;
+}
+
+template <int BN, int S>
+int noalloc_launch(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K, const TcEpilogue &ep,
+                   DeviceControl *ctrl, cudaStream_t s) {
+  using Cfg = TcCfg<BN, S>;
+  if (cudaFuncSetAttribute(tc_gemm_kernel<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) !=
+      cudaSuccess)
+    return PURL_ERR_CUDA;
+  long long tiles = (long long)ceil_div(M, TC_BM) * ceil_div(N, BN);
+  if (tiles > 0x7fffffffLL) return PURL_ERR_UNSUPPORTED;
+  TcView v0{0, 0};
+  tc_gemm_kernel<BN, S><<<dim3((unsigned)tiles, 1), TC_THREADS, Cfg::SMEM, s>>>(ma, mb, v0, v0, M, N, K,
+                                                                                 ceil_div(K, TC_BK) * TC_BK, ep, ctrl);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
+}  // namespace
+
+}  // namespace purl
+
+extern "C" int purl_gemm_tc_noalloc(char transa, char transb, int m, int n, int k, double alpha, const double *A,
+                                    int lda, const double *B, int ldb, double beta, double *C, int ldc, int slices,
+                                    cudaStream_t stream) {
+  using namespace purl;
+  const bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
+  if (!ta && transa != 'N' && transa != 'n') return -1;
+  if (!tb && transb != 'N' && transb != 'n') return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  const int arows = ta ? k : m, brows = tb ? n : k;
+  if (!A && (long long)m * k > 0) return -7;
+  if (lda < (arows > 1 ? arows : 1)) return -8;
+  if (!B && (long long)k * n > 0) return -9;
+  if (ldb < (brows > 1 ? brows : 1)) return -10;
+  if (!C && (long long)m * n > 0) return -12;
+  if (ldc < (m > 1 ? m : 1)) return -13;
+  if (slices < 1 || slices > 3) return -14;
+  // the operand slices must fit in the static scratch (after the status word)
+  const size_t ea = slice_elems(k > 0 ? k : 1, m > 0 ? m : 1, slices);
+  const size_t eb = slice_elems(k > 0 ? k : 1, n > 0 ? n : 1, slices);
+  const size_t off_a = 256, off_b = off_a + align_up(ea * sizeof(__nv_bfloat16), 256);
+  if (off_b + align_up(eb * sizeof(__nv_bfloat16), 256) > kNoAllocScratchBytes) return PURL_ERR_NOMEM;
+  if ((long long)m * n == 0) return PURL_OK;
+  NoAllocDevice *nd = nullptr;
+  PURL_TRY(noalloc_setup(&nd));
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PURL_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PURL_ERR_CUDA;
+  if (k == 0) {
+    long long g = ((long long)m * n + 255) / 256;
+    if (g > (long long)sms * 16) g = (long long)sms * 16;
+    noalloc_scale_kernel<<<(int)g, 256, 0, stream>>>(m, n, beta, C, ldc);
+    return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+  }
+  DeviceControl *ctrl = reinterpret_cast<DeviceControl *>(nd->scratch);
+  Slices sa = make_slices(reinterpret_cast<__nv_bfloat16 *>(nd->scratch + off_a), k, m, slices);
+  Slices sb = make_slices(reinterpret_cast<__nv_bfloat16 *>(nd->scratch + off_b), k, n, slices);
+  // operand A: rows K, cols M (K-major); operand B: rows K, cols N
+  auto split = [&](bool transposed, int R, int Cc, const double *X, long long ldx, Slices dst) -> int {
+    if (transposed) {
+      dim3 grid(ceil_div(R, 32), ceil_div(Cc, 32));
+      if (grid.y > 65535) return PURL_ERR_UNSUPPORTED;
+      split_t_kernel<<<grid, dim3(32, 8), 0, stream>>>(R, Cc, X, ldx, dst);
+    } else {
+      long long g = ((long long)R * Cc + 255) / 256;
+      if (g > (long long)sms * 16) g = (long long)sms * 16;
+      split_kernel<<<(int)g, 256, 0, stream>>>(R, Cc, X, ldx, dst);
+    }
+    return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+  };
+  if (ta) PURL_TRY(split(false, k, m, A, lda, sa));
+  else PURL_TRY(split(true, m, k, A, lda, sa));
+  if (tb) PURL_TRY(split(true, n, k, B, ldb, sb));
+  else PURL_TRY(split(false, k, n, B, ldb, sb));
+  int BN = n > 128 ? 256 : (n > 64 ? 128 : (n > 32 ? 64 : 32));
+  if (slices == 3 && BN > 128) BN = 128;
+  CUtensorMap ma, mb;
+  PURL_TRY(make_map(&ma, sa, k, m, TC_BM));
+  PURL_TRY(make_map(&mb, sb, k, n, BN));
+  TcEpilogue ep;
+  ep.mode = 0;
+  ep.alpha = alpha;
+  ep.beta = beta;
+  ep.C = C;
+  ep.ldc = ldc;
+#define PURL_NA_CASE(BN_, S_) \
+  if (BN == BN_ && slices == S_) return noalloc_launch<BN_, S_>(ma, mb, m, n, k, ep, ctrl, stream);
+  PURL_NA_CASE(32, 1) PURL_NA_CASE(64, 1) PURL_NA_CASE(128, 1) PURL_NA_CASE(256, 1)
+  PURL_NA_CASE(32, 2) PURL_NA_CASE(64, 2) PURL_NA_CASE(128, 2) PURL_NA_CASE(256, 2)
+  PURL_NA_CASE(32, 3) PURL_NA_CASE(64, 3) PURL_NA_CASE(128, 3)
+#undef PURL_NA_CASE
+  return PURL_ERR_UNSUPPORTED;
+}
+
+namespace purl {
+
 }  // namespace purl
