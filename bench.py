@@ -181,6 +181,22 @@ def run_reference(a):
 
 
 # ---------------------------------------------------------------- ours -----
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank timing over the process group (a plain host value when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(flops_per_step: float, world: int, ms_step_max: float) -> float:
+    """Whole-job TFLOP/s of N independent replicas (weak scaling): all ranks' work over the slowest rank."""
+    return flops_per_step * world / (ms_step_max * 1e-3) / 1e12
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -241,13 +257,10 @@ def run_ours(a):
     prof = B.purl_profile_read() if not a.no_profile else None
     prof_named = B.purl_profile_read_named() if not a.no_profile else None
     B.purl_profile_enable(False)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dev)
     ms_step = ms_total / a.steps
     flops = urv_flops(m, n, q, reorth)
-    value = flops * world / (ms_step * 1e-3) / 1e12
+    value = replica_value(flops, world, ms_step)
 
     # ---- errors of the last factorization (random-probe estimators, FP64) ----
     errs = probe_errors(A, U, R, V)
@@ -376,12 +389,7 @@ def end_to_end(a, A, U, R, V, ws, mode, seed, world, dev, B):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
     return {"value": urv_flops(m, n, a.q, a.reorth) * world / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
             "ms_per_step": ms, "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * (m * n + 2 * n * n),
             "steps": steps}

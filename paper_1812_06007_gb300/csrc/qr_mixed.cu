@@ -194,24 +194,20 @@ __global__ void split_rows_t_kernel(int rows, int nbw, const double *__restrict_
 
 // W2(:, c) = sum_z Pd_z(c, :)^T (nbw <= QR_NB entries), sliced with its own
 // exponent.  Block = 32 columns x 8 row groups; thread (cx, ry) owns rows
-// ry, ry + 8, ... of column cx.
+// ry, ry + 8, ... of column cx; two passes over the partials (maximum, then
+// digits) keep the registers free.
 __global__ void __launch_bounds__(256) reduce_slices_kernel(int nbw, int nc, int splits, const double *__restrict__ Pd,
                                                             Slices W2s) {
-  constexpr int RPT = QR_NB / 8;
   __shared__ unsigned long long mxs[8][32];
   const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + cx;
-  double v[RPT];
   unsigned long long mx = 0;
-#pragma unroll
-  for (int q = 0; q < RPT; ++q) {
-    const int r = ry + 8 * q;
-    double a = 0.0;
-    if (c < nc && r < nbw)
+  if (c < nc)
+    for (int r = ry; r < nbw; r += 8) {
+      double a = 0.0;
       for (int z = 0; z < splits; ++z) a += Pd[(long long)z * nc * nbw + c + (long long)r * nc];
-    v[q] = a;
-    mx = max(mx, abs_bits(a));
-  }
+      mx = max(mx, abs_bits(a));
+    }
   mxs[ry][cx] = mx;
   __syncthreads();
   unsigned long long m = 0;
@@ -220,10 +216,10 @@ __global__ void __launch_bounds__(256) reduce_slices_kernel(int nbw, int nc, int
   const int e = exp_above_bits(m);
   if (c >= nc) return;
   if (ry == 0) W2s.scale[c] = e;
-#pragma unroll
-  for (int q = 0; q < RPT; ++q) {
-    const int r = ry + 8 * q;
-    if (r < nbw) write_fixed_slices(v[q], e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
+  for (int r = ry; r < nbw; r += 8) {
+    double a = 0.0;
+    for (int z = 0; z < splits; ++z) a += Pd[(long long)z * nc * nbw + c + (long long)r * nc];
+    write_fixed_slices(a, e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
   }
 }
 
@@ -421,7 +417,8 @@ int outer_apply(int rows, int nbw, int nc, double *Cp, int ldc, const Slices &Cs
   vt.C = w.Vtl;
   vt.ldc = m;
   vt.tag = "tcx outer V~ = V T";
-  PURL_TRY(tcx_gemm_view(w.Vots, 0, 0, w.Ts, 0, 0, rows, nbw, nbw, w.S, vt, 1, kChunkAlign, s));
+  PURL_TRY(tcx_gemm_view(w.Vots, 0, 0, w.Ts, 0, 0, rows, nbw, nbw, w.S, vt, 1,
+                         ceil_div(nbw, kChunkAlign) * kChunkAlign, s));
   PURL_TRY(split_exact(rows, nbw, w.Vtl, m, w.Vtls, nullptr, s));
   // re-slice the active block with fresh per-column exponents
   Slices view = Cs;

@@ -6,7 +6,7 @@
 
 namespace purl {
 
-constexpr int QR_NB = 256;  // outer block: QR_NB / QR_B inner panels share one aggregated update
+constexpr int QR_NB = 512;  // outer block: QR_NB / QR_B inner panels share one aggregated update
 
 struct QrMixWork {
   QrWork base;       // tau, T, panel V (FP64), panel scratch, Gram partials
