@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
                                                     unsigned *counter, DeviceControl *ctrl) {
   extern __shared__ double Ps[];  // ch x QR_B, column-major (column t at Ps + t*ch)
   __shared__ double s_w[QR_B];
-  __shared__ double s_par[3];     // beta, v0, tau
+  __shared__ double s_par[4];     // beta, v0, tau, 1/v0
   const int P = gridDim.x;
   const int c = blockIdx.x;
   const int r0 = c * ch;
@@ -91,20 +91,20 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
       double sigma = s_w[k];
       double x0 = __ldcg(&rk[k]);
       if (sigma == 0.0) {
-        s_par[0] = x0; s_par[1] = 1.0; s_par[2] = 0.0;
+        s_par[0] = x0; s_par[1] = 1.0; s_par[2] = 0.0; s_par[3] = 1.0;
       } else {
         double norm = sqrt(x0 * x0 + sigma);
         double beta = (x0 >= 0.0) ? -norm : norm;
-        s_par[0] = beta; s_par[1] = x0 - beta; s_par[2] = (beta - x0) / beta;
+        s_par[0] = beta; s_par[1] = x0 - beta; s_par[2] = (beta - x0) / beta; s_par[3] = 1.0 / (x0 - beta);
       }
       if (c == 0) tau[k] = s_par[2];
     }
     __syncthreads();
-    const double beta = s_par[0], v0 = s_par[1], tk = s_par[2];
+    const double beta = s_par[0], tk = s_par[2], inv_v0 = s_par[3];
     if (tk != 0.0) {
-      // w_t = tau (a_kt + v(k+1:)^T a_t) with v(k+1:) = x(k+1:)/v0
-      for (int t = k + 1 + tid; t < bw; t += PNT) s_w[t] = tk * (__ldcg(&rk[t]) + s_w[t] / v0);
-      for (int i = i_lo + tid; i < nr; i += PNT) Ps[k * ch + i] /= v0;
+      // w_t = tau (a_kt + v(k+1:)^T a_t) with v(k+1:) = x(k+1:)/v0 (one division, then products)
+      for (int t = k + 1 + tid; t < bw; t += PNT) s_w[t] = tk * (__ldcg(&rk[t]) + s_w[t] * inv_v0);
+      for (int i = i_lo + tid; i < nr; i += PNT) Ps[k * ch + i] *= inv_v0;
       __syncthreads();
       if (k >= r0 && k < r0 + nr && tid == 0) Ps[k * ch + (k - r0)] = beta;
       const int ncol = bw - k - 1;
@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(256) larft_kernel(int bw, int splits, const do
                                                     const double *tau, double *T, bool tau_from_gram) {
   __shared__ double Gm[QR_B][QR_B + 1];
   __shared__ double Ts[QR_B][QR_B + 1];
+  __shared__ double tks[QR_B];
   for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) {
     int i = e % bw, j = e / bw;
     double s = 0.0;
@@ -149,9 +150,16 @@ __global__ void __launch_bounds__(256) larft_kernel(int bw, int splits, const do
     Ts[i][j] = 0.0;
   }
   __syncthreads();
-  for (int k = 0; k < bw; ++k) {
+  // the tau_k, each computed once (an FP64 division is a long sequence)
+  if (threadIdx.x < bw) {
+    const int k = threadIdx.x;
     double tk = tau[k];
     if (tau_from_gram && tk != 0.0) tk = 2.0 / Gm[k][k];
+    tks[k] = tk;
+  }
+  __syncthreads();
+  for (int k = 0; k < bw; ++k) {
+    const double tk = tks[k];
     int i = threadIdx.x;
     double s = 0.0;
     if (i < k)
