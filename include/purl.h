@@ -95,6 +95,35 @@ int purl_urv_factor_ex(int m, int n, const double *A, int lda, int q, int reorth
 size_t purl_urv_workspace_bytes(int m, int n, int mode);
 
 /*
+ * purl_urv_backward -- reverse mode of the FP64 map A -> (U, R, V) of
+ * purl_urv_factor (Section 3, Eqs. (5)-(6)) with the Gaussian G held fixed:
+ * Abar = J^T (Ubar, Rbar, Vbar), the gradient with respect to A of
+ * <Ubar, U> + <Rbar, R> + <Vbar, V>.  The paper defines no derivative; this
+ * is the chain rule through every product and every QR of the forward pass,
+ * with the thin-QR reverse rule (diag(R) > 0)
+ *   Mbar = (Qbar + Q copyltu(R Rbar^T - Qbar^T Q)) R^{-T},
+ *   copyltu(X) = lower triangle of X mirrored onto the upper one,
+ * applied to the QRs of Eqs. (5) and (6) and, when `reorth` is set, to every
+ * re-orthonormalisation; power-step products are reversed with transposed
+ * products.  The forward iterates are recomputed from A and `seed` inside the
+ * call (nothing is kept from a forward call).
+ *   m, n, A, lda, q, reorth, seed   as for purl_urv_factor (same G).
+ *   Ubar (m x n, ldub), Rbar (n x n, ldrb; only its upper triangle matters,
+ *   R's lower triangle being identically zero), Vbar (n x n, ldvb): inputs.
+ *   Abar (m x n, ldab): output, overwritten.
+ * Requires A V, the power iterates and Y_q to have full column rank (R^{-T}
+ * exists); otherwise the result is not finite.  Workspace as for
+ * purl_urv_factor_ex (purl_urv_backward_workspace_bytes; NULL = allocate
+ * stream-ordered on `stream`).  Errors: -i for bad argument i,
+ * PURL_ERR_SHAPE for m < n, PURL_ERR_NOMEM, PURL_ERR_CUDA.
+ */
+int purl_urv_backward(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                      const double *Ubar, int ldub, const double *Rbar, int ldrb,
+                      const double *Vbar, int ldvb, double *Abar, int ldab, void *workspace,
+                      size_t workspace_bytes, cudaStream_t stream);
+size_t purl_urv_backward_workspace_bytes(int m, int n, int q);
+
+/*
  * purl_gaussian -- the Gaussian matrix G of Section 3 (the paper fixes no
  * generator; this library's is defined here).  Element e of the rows x cols
  * matrix, e = i + j*rows (column-major linear index), is word e%4 of the

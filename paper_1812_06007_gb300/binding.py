@@ -35,6 +35,8 @@ SIGNATURES = {
     "purl_urv_factor": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _p]),
     "purl_urv_factor_ex": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
     "purl_urv_workspace_bytes": (_sz, [_i, _i, _i]),
+    "purl_urv_backward": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _p, _i, _p, _sz, _p]),
+    "purl_urv_backward_workspace_bytes": (_sz, [_i, _i, _i]),
     "purl_gaussian": (_i, [_u64, _u64, _i, _i, _p, _i, _p]),
     "purl_qr": (_i, [_i, _i, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
     "purl_qr_workspace_bytes": (_sz, [_i, _i, _i]),
@@ -168,6 +170,26 @@ def purl_urv_factor(A, q: int, reorth: bool, seed: int, mode: int = PURL_MODE_FP
 
 def purl_urv_workspace_bytes(m: int, n: int, mode: int = PURL_MODE_FP64) -> int:
     return int(lib().purl_urv_workspace_bytes(m, n, mode))
+
+
+def purl_urv_backward(A, q: int, reorth: bool, seed: int, Ubar, Rbar, Vbar, out=None, workspace=None,
+                      stream=None):
+    """Abar = J^T (Ubar, Rbar, Vbar) for the FP64 map A -> (U, R, V) of purl_urv_factor (G fixed by seed)."""
+    _cuda_check(A, Ubar, Rbar, Vbar)
+    m, n = A.shape
+    Abar = out if out is not None else empty_colmajor(m, n, A.device)
+    _cuda_check(Abar)
+    ws_ptr, ws_bytes = (_ptr(workspace), workspace.numel() * workspace.element_size()) if workspace is not None \
+        else (ctypes.c_void_p(0), 0)
+    st = lib().purl_urv_backward(m, n, _ptr(A), _ld(A), q, int(bool(reorth)), seed, _ptr(Ubar), _ld(Ubar),
+                                 _ptr(Rbar), _ld(Rbar), _ptr(Vbar), _ld(Vbar), _ptr(Abar), _ld(Abar), ws_ptr,
+                                 ws_bytes, _stream(stream))
+    _check("purl_urv_backward", st)
+    return Abar
+
+
+def purl_urv_backward_workspace_bytes(m: int, n: int, q: int) -> int:
+    return int(lib().purl_urv_backward_workspace_bytes(m, n, q))
 
 
 def purl_qr(M, mode: int = PURL_MODE_FP64, want_q: bool = True, want_r: bool = True, stream=None):

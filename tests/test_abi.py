@@ -63,6 +63,11 @@ def test_argument_errors_are_reported_before_device_work(purl):
     assert L.purl_gemm_f64(b"X", b"N", 1, 1, 1, 1.0, fake, 1, fake, 1, 0.0, fake, 1, nul) == -1
     assert L.purl_urv_truncate(4, 4, 5, fake, 4, fake, 4, fake, 4, fake, 4, nul) == -3
     assert L.purl_qr(2, 3, fake, 2, fake, 2, fake, 3, 0, nul, 0, nul) == purl.PURL_ERR_SHAPE
+    assert L.purl_urv_backward(3, 5, nul, 3, 1, 1, 7, nul, 3, nul, 5, nul, 5, nul, 3, nul, 0, nul) == \
+        purl.PURL_ERR_SHAPE
+    assert L.purl_urv_backward(4, 4, fake, 4, 1, 1, 7, nul, 4, fake, 4, fake, 4, fake, 4, nul, 0, nul) == -8
+    assert L.purl_urv_backward(4, 4, fake, 4, 1, 1, 7, fake, 4, fake, 4, fake, 4, fake, 3, nul, 0, nul) == -15
+    assert L.purl_urv_backward_workspace_bytes(4, 4, -1) == 0
     # empty problems are valid no-ops
     assert L.purl_urv_factor(0, 0, nul, 1, 1, 1, 7, nul, 1, nul, 1, nul, 1, nul) == 0
     assert L.purl_urv_factor(5, 0, nul, 5, 1, 1, 7, nul, 5, nul, 1, nul, 1, nul) == 0
