@@ -124,6 +124,84 @@ int purl_urv_backward(int m, int n, const double *A, int lda, int q, int reorth,
 size_t purl_urv_backward_workspace_bytes(int m, int n, int q);
 
 /*
+ * Batched PowerURV in FP32 (Section 3, Eqs. (5)-(6), for many independent
+ * small matrices).  The paper factors one matrix at a time; this engine runs
+ * thousands in one persistent launch: every CTA takes the next matrix from a
+ * queue and carries out the whole algorithm on it (Gaussian G, q power steps
+ * with Householder re-orthonormalisation, the QR of Eq. (5), A V, the QR of
+ * Eq. (6)), all in FP32 arithmetic with FP32 storage.  Same sign convention
+ * as purl_urv_factor: every QR has a nonnegative R diagonal.
+ *
+ * One descriptor per matrix, in DEVICE memory, column-major FP32 matrices:
+ *   m, n      1 <= n <= m <= max_m (<= 1024), n <= max_n (<= 512)
+ *   A, lda    input (not modified);  U, ldu (m x n), R, ldr (n x n, zeros
+ *             below the diagonal), V, ldv (n x n): outputs, caller-owned,
+ *             not aliasing A or each other
+ *   seed      key of this matrix's G: element e (column-major) of the n x n
+ *             G is drawn as in purl_gaussian (Philox4x64-10, stream 0, the
+ *             same 53-bit uniforms) with Box-Muller evaluated in FP32.
+ * Matrices are taken in array order; putting the costliest (largest m n^2)
+ * first balances the grid.  A descriptor outside the limits is skipped and
+ * makes purl_urv_batched_status return PURL_ERR_UNSUPPORTED.
+ */
+typedef struct purl_batch_item {
+  int m, n;
+  int lda, ldu, ldr, ldv;
+  const float *A;
+  float *U, *R, *V;
+  uint64_t seed;
+} purl_batch_item;
+
+/* Number of kernel variants (panel width x CTAs per SM) of the batched engine. */
+int purl_urv_batched_variants(void);
+
+/* Workspace bytes for variant v (0 .. variants-1), or for any variant when
+ * v < 0; 0 on bad arguments or when the variant cannot run with max_m. */
+size_t purl_urv_batched_workspace_bytes(int max_m, int max_n, int variant);
+
+/*
+ * purl_urv_factor_batched -- factor `count` matrices described by `items`
+ * (device array) with q power steps (reorth as in purl_urv_factor).
+ * variant < 0 uses the variant purl_urv_batched_autotune chose for the same
+ * (count, max_m, max_n, q, reorth) on this device, else the first variant
+ * that fits.  Workspace: device memory, 256-byte aligned, at least
+ * purl_urv_batched_workspace_bytes(max_m, max_n, variant) bytes; its first
+ * 256 bytes hold the queue position, reset by a kernel at the start of each
+ * call, so one workspace must not serve two calls in flight at once.
+ * Enqueues two kernels and nothing else (no allocation, no host sync), so the
+ * call can be captured in a CUDA graph once an uncaptured call with the same
+ * variant and max_m has run (that first call sets the kernel's shared-memory
+ * limit).  Errors: -i for bad argument i, PURL_ERR_NOMEM (workspace),
+ * PURL_ERR_UNSUPPORTED, PURL_ERR_CUDA.
+ */
+int purl_urv_factor_batched(int count, const purl_batch_item *items, int max_m, int max_n, int q,
+                            int reorth, int variant, void *workspace, size_t workspace_bytes,
+                            cudaStream_t stream);
+
+/* Synchronises `stream` and returns the device-side status of the last
+ * batched call on `workspace` (PURL_OK or PURL_ERR_UNSUPPORTED). */
+int purl_urv_batched_status(void *workspace, cudaStream_t stream);
+
+/*
+ * purl_urv_batched_autotune -- runs every variant whose workspace fits in
+ * `workspace_bytes` on the given batch (one warm-up and one timed run each,
+ * CUDA events on `stream`; synchronises), remembers the fastest for later
+ * calls with variant < 0, and returns it in *variant_out and its time in
+ * *ms_out (either may be NULL).  The outputs of the batch are overwritten.
+ */
+int purl_urv_batched_autotune(int count, const purl_batch_item *items, int max_m, int max_n, int q,
+                              int reorth, void *workspace, size_t workspace_bytes, cudaStream_t stream,
+                              int *variant_out, float *ms_out);
+
+/*
+ * purl_gaussian_f32 -- the FP32 Gaussian draw of the batched engine: the
+ * 53-bit uniforms of purl_gaussian rounded once to FP32, then Box-Muller in
+ * FP32 (logf, sincospif).  Layout and arguments as purl_gaussian.
+ */
+int purl_gaussian_f32(uint64_t seed, uint64_t stream_id, int rows, int cols, float *G, int ldg,
+                      cudaStream_t stream);
+
+/*
  * purl_gaussian -- the Gaussian matrix G of Section 3 (the paper fixes no
  * generator; this library's is defined here).  Element e of the rows x cols
  * matrix, e = i + j*rows (column-major linear index), is word e%4 of the

@@ -6,4 +6,4 @@ with the same entry-point names; ``workloads`` synthesises seeded inputs.
 Nothing here falls back to the CPU: if the library is missing, the binding
 raises.
 """
-__all__ = ["binding", "workloads", "autograd"]
+__all__ = ["binding", "workloads", "autograd", "batched"]

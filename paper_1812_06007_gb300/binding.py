@@ -37,6 +37,13 @@ SIGNATURES = {
     "purl_urv_workspace_bytes": (_sz, [_i, _i, _i]),
     "purl_urv_backward": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _p, _i, _p, _sz, _p]),
     "purl_urv_backward_workspace_bytes": (_sz, [_i, _i, _i]),
+    "purl_urv_batched_variants": (_i, []),
+    "purl_urv_batched_workspace_bytes": (_sz, [_i, _i, _i]),
+    "purl_urv_factor_batched": (_i, [_i, _p, _i, _i, _i, _i, _i, _p, _sz, _p]),
+    "purl_urv_batched_status": (_i, [_p, _p]),
+    "purl_urv_batched_autotune": (_i, [_i, _p, _i, _i, _i, _i, _p, _sz, _p, ctypes.POINTER(_i),
+                                       ctypes.POINTER(ctypes.c_float)]),
+    "purl_gaussian_f32": (_i, [_u64, _u64, _i, _i, _p, _i, _p]),
     "purl_gaussian": (_i, [_u64, _u64, _i, _i, _p, _i, _p]),
     "purl_qr": (_i, [_i, _i, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
     "purl_qr_workspace_bytes": (_sz, [_i, _i, _i]),
@@ -190,6 +197,55 @@ def purl_urv_backward(A, q: int, reorth: bool, seed: int, Ubar, Rbar, Vbar, out=
 
 def purl_urv_backward_workspace_bytes(m: int, n: int, q: int) -> int:
     return int(lib().purl_urv_backward_workspace_bytes(m, n, q))
+
+
+class BatchItem(ctypes.Structure):
+    """purl_batch_item of include/purl.h (64 bytes)."""
+    _fields_ = [("m", _i), ("n", _i), ("lda", _i), ("ldu", _i), ("ldr", _i), ("ldv", _i),
+                ("A", _p), ("U", _p), ("R", _p), ("V", _p), ("seed", _u64)]
+
+
+def purl_gaussian_f32(seed: int, rows: int, cols: int, stream_id: int = 0, out=None, stream=None):
+    torch = _torch()
+    G = out if out is not None else empty_colmajor(rows, cols, dtype=torch.float32)
+    if not G.is_cuda or G.dtype != torch.float32:
+        raise ValueError("expected a CUDA float32 tensor")
+    _check("purl_gaussian_f32", lib().purl_gaussian_f32(seed, stream_id, rows, cols, _ptr(G), _ld(G),
+                                                        _stream(stream)))
+    return G
+
+
+def purl_urv_batched_variants() -> int:
+    return int(lib().purl_urv_batched_variants())
+
+
+def purl_urv_batched_workspace_bytes(max_m: int, max_n: int, variant: int = -1) -> int:
+    return int(lib().purl_urv_batched_workspace_bytes(max_m, max_n, variant))
+
+
+def purl_urv_factor_batched(items, count: int, max_m: int, max_n: int, q: int, reorth: bool, workspace,
+                            variant: int = -1, stream=None):
+    """items: device tensor holding `count` BatchItem records; workspace: device tensor."""
+    st = lib().purl_urv_factor_batched(count, _ptr(items), max_m, max_n, q, int(bool(reorth)), variant,
+                                       _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                       _stream(stream))
+    _check("purl_urv_factor_batched", st)
+
+
+def purl_urv_batched_status(workspace, stream=None) -> int:
+    return int(lib().purl_urv_batched_status(_ptr(workspace), _stream(stream)))
+
+
+def purl_urv_batched_autotune(items, count: int, max_m: int, max_n: int, q: int, reorth: bool, workspace,
+                              stream=None):
+    """(variant, ms) of the fastest variant on this batch; remembered for variant=-1 calls."""
+    v = ctypes.c_int(-1)
+    ms = ctypes.c_float(0.0)
+    st = lib().purl_urv_batched_autotune(count, _ptr(items), max_m, max_n, q, int(bool(reorth)), _ptr(workspace),
+                                         workspace.numel() * workspace.element_size(), _stream(stream),
+                                         ctypes.byref(v), ctypes.byref(ms))
+    _check("purl_urv_batched_autotune", st)
+    return v.value, ms.value
 
 
 def purl_qr(M, mode: int = PURL_MODE_FP64, want_q: bool = True, want_r: bool = True, stream=None):

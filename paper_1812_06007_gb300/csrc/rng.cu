@@ -6,23 +6,11 @@
 // embarrassingly parallel, then Box-Muller for the normal deviates.
 #include "common.cuh"
 #include "profile.cuh"
+#include "rng.cuh"
 
 namespace purl {
 
 namespace {
-
-__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
-  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
-  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
-    uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
-    uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
-    k0 += W0; k1 += W1;  // the bump after the last round is unused
-  }
-}
 
 __device__ __forceinline__ double u53(uint64_t x) {
   return (static_cast<double>(x >> 11) + 0.5) * 0x1.0p-53;

@@ -26,6 +26,7 @@ SEED_U = 1001   # left Haar factor
 SEED_V = 1002   # right Haar factor
 SEED_G = 7      # PowerURV's Gaussian start matrix (Philox key)
 SEED_B = 9      # target matrix of the adjoint loss
+SEED_BATCH = 10000  # batched matrix i: Haar factors and G keyed by SEED_BATCH + i
 
 
 def sigma_profile(kind: str, n: int, decades: float = 8.0, power: float = 2.0,
@@ -124,3 +125,35 @@ def gaussian_matrix_torch(m: int, n: int, seed: int, device="cuda"):
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
     return torch.randn(n, m, generator=gen, device=device, dtype=torch.float64).t()
+
+
+# ------------------------------------------------------------ batched ------
+def batched_shapes(count: int, seed: int = SEED_BATCH, n_lo: int = 16, n_hi: int = 256):
+    """Sizes of the batched workload: n ~ U[n_lo, n_hi], m ~ U[n, 2n] (integers)."""
+    rng = np.random.default_rng(seed)
+    n = rng.integers(n_lo, n_hi + 1, size=count)
+    m = np.array([int(rng.integers(k, 2 * k + 1)) for k in n], dtype=np.int64)
+    return m.astype(np.int64), n.astype(np.int64)
+
+
+def _haar_gen(rng, rows: int, cols: int) -> np.ndarray:
+    Q, R = np.linalg.qr(rng.standard_normal((rows, cols)))
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return Q * d
+
+
+def batched_matrix_np(m: int, n: int, index: int, decades: float = 6.0) -> np.ndarray:
+    """Matrix `index` of the batch: Uh diag(10^(-decades (j-1)/(n-1))) Vh^T in
+    FP32 (column-major), Uh (m x n) and Vh (n x n) Haar with seeds derived
+    from SEED_BATCH + index."""
+    key = SEED_BATCH + index
+    Uh = _haar_gen(np.random.default_rng([key, 1]), m, n)
+    Vh = _haar_gen(np.random.default_rng([key, 2]), n, n)
+    sig = 10.0 ** (-decades * np.arange(n) / max(n - 1, 1))
+    return np.asfortranarray(((Uh * sig) @ Vh.T).astype(np.float32))
+
+
+def batched_seed(index: int) -> int:
+    """Philox key of matrix `index`'s Gaussian start matrix G."""
+    return SEED_BATCH + index
