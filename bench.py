@@ -3,6 +3,12 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--mode mixed|fp64] [--m M] [--n N] [--q Q] [--no-reorth]
+                    [--workload urv|batched|adjoint]
+
+--workload batched times the batched FP32 engine (4096 matrices, n ~ U[16,256],
+m ~ U[n,2n], q = 2, one persistent launch) in matrices/s; --workload adjoint
+times the FP64 reverse mode (m = n = 2048, q = 2) in seconds per backward.
+The default is the PowerURV factorization below.
 
 A step is one full PowerURV factorization A = U R V^T (Section 3 of the
 paper): Gaussian draw, q power steps with re-orthonormalisation, the QR of
@@ -68,6 +74,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip per-kernel event timing")
+    ap.add_argument("--workload", choices=["urv", "batched", "adjoint"], default="urv")
+    ap.add_argument("--count", type=int, default=4096, help="batched: number of matrices")
     ap.add_argument("--fp64-n", type=int, default=8192,
                     help="size of the FP64-path comparison run (0 = skip); FP64 at n=16384 takes minutes")
     a = ap.parse_args()
@@ -447,8 +455,382 @@ def roofline(prof, named, steps, mode):
     return base
 
 
+
+# ------------------------------------------------------------- batched -----
+BATCHED_METRIC = "batched PowerURV FP32 matrices/s (4096 matrices, n~U[16,256], m~U[n,2n], q=2)"
+# FP32 FFMA peak: 152 SMs x 128 FP32 lanes x 2 flops per clock at the SM clock
+# sampled under load (1920 MHz if no sample).
+FP32_LANES = 152 * 128
+
+
+def _batched_inputs(count, ms, ns):
+    """Packed host FP32 A of the batched workload, built in a spawn pool (numpy QR per matrix)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import numpy as np
+    from paper_1812_06007_gb300 import workloads as W
+    jobs = [(int(ms[i]), int(ns[i]), i) for i in range(count)]
+    workers = max(1, min(16, os.cpu_count() or 1))
+    # one BLAS thread per worker: the spawned processes inherit this environment
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            mats = list(ex.map(_batched_one, jobs, chunksize=64))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return mats
+
+
+def _batched_one(job):
+    from paper_1812_06007_gb300 import workloads as W
+    m, n, i = job
+    return W.batched_matrix_np(m, n, i)
+
+
+def run_batched(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1812_06007_gb300 import binding as B
+    from paper_1812_06007_gb300 import build as Bld
+    from paper_1812_06007_gb300 import workloads as W
+    from paper_1812_06007_gb300.batched import Batch, flops as batch_flops
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    count, q, reorth = a.count, a.q, a.reorth
+    ms, ns = W.batched_shapes(count)
+    # weak scaling: every rank factors its own batch of `count` matrices (seeds offset by rank)
+    mats = _batched_inputs(count, ms, ns)   # spawn pool before any GPU call
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Bld.build()
+    B.lib()
+    b = Batch(ms, ns, [W.batched_seed(i) + rank * count for i in range(count)], device=dev)
+    host = b.pack_host(mats)
+    b.load_packed_a(host)
+    stream = torch.cuda.current_stream()
+    variant, tune_ms = b.autotune(q, reorth, stream=stream)
+    for _ in range(a.warmup):
+        b.factor(q, reorth, stream=stream)
+    torch.cuda.synchronize()
+    if b.status() != 0:
+        raise RuntimeError("batched status not ok after warm-up")
+    # the step as a CUDA graph (reset + persistent kernel), replayed K times
+    gs = torch.cuda.Stream(device=dev)
+    gs.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(gs):
+        b.factor(q, reorth, stream=gs)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=gs):
+            b.factor(q, reorth, stream=gs)
+    torch.cuda.synchronize()
+    launches0 = B.purl_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk, torch.cuda.stream(gs):
+        e0.record(gs)
+        for _ in range(a.steps):
+            g.replay()
+        e1.record(gs)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = 2 * a.steps  # each replay runs the graph's two kernels (counted at capture)
+    assert B.purl_launch_count() == launches0
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
+    value = count * world / (ms_step * 1e-3)
+    F = batch_flops(ms, ns, q, reorth)
+    # per-matrix launches of the same device code (the baseline the single launch
+    # replaces), timed on every 16th descriptor and scaled by its share of the m n^2 work
+    ws = b.ensure_workspace(-1)
+    torch.cuda.synchronize()
+    sample = list(range(0, b.count, 16))
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for d in sample:
+        B.purl_urv_factor_batched(b.item_view(d), 1, b.max_m, b.max_n, q, reorth, ws, variant=variant,
+                                  stream=stream)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    work = (ms * ns * ns).astype(np.float64)[b.order]
+    per_matrix_ms = p0.elapsed_time(p1) * work.sum() / work[sample].sum()
+    # uncaptured launches of the persistent kernel (no graph)
+    u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    u0.record(stream)
+    for _ in range(a.steps):
+        b.factor(q, reorth, stream=stream)
+    u1.record(stream)
+    torch.cuda.synchronize()
+    nograph_ms = u0.elapsed_time(u1) / a.steps
+    # end to end: packed A host -> device, factor, U R V device -> host, every step
+    hA = torch.from_numpy(host).pin_memory()
+    hU = torch.empty(b.U.numel(), dtype=torch.float32).pin_memory()
+    hR = torch.empty(b.R.numel(), dtype=torch.float32).pin_memory()
+    hV = torch.empty(b.V.numel(), dtype=torch.float32).pin_memory()
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    e2e_steps = max(1, min(a.steps, 3))
+    for _ in range(e2e_steps):
+        b.A.copy_(hA, non_blocking=True)
+        b.factor(q, reorth, stream=stream)
+        hU.copy_(b.U, non_blocking=True)
+        hR.copy_(b.R, non_blocking=True)
+        hV.copy_(b.V, non_blocking=True)
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(x0.elapsed_time(x1) / e2e_steps, dev)
+    if b.status() != 0:
+        raise RuntimeError("batched status not ok")
+    # errors on a sample (FP64 products on the device)
+    worst_rec = 0.0
+    for i in list(range(0, count, max(1, count // 64))):
+        A_ = b.a(i).double()
+        worst_rec = max(worst_rec, float(torch.linalg.matrix_norm(A_ - b.u(i).double() @ b.r(i).double()
+                                                                   @ b.v(i).double().t())
+                                         / torch.linalg.matrix_norm(A_)))
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    csum = clk.summary()
+    mhz = csum.get("sm_mhz") or 1920.0
+    fp32_peak = FP32_LANES * 2 * mhz * 1e6 / 1e12
+    achieved = F / (ms_step * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "urv_batched_kernel", "achieved": achieved, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+            "peak_source": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flops x {mhz:.0f} MHz (sampled SM clock)",
+            "flops_counted": "algorithmic PowerURV flops of every matrix (explicit Q counted)",
+            "launches_per_step": 2, "avg_launch_ms": ms_step}
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        cpu = _batched_cpu(mats, ms, ns, q, reorth)
+    line = {
+        "metric": BATCHED_METRIC, "value": value, "unit": "matrices/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched PowerURV, {count} matrices, n~U[16,256], m~U[n,2n], q={q} "
+                               f"reorth={int(reorth)}, FP32", "count": count, "q": q, "reorth": reorth,
+                   "sigma": "10^(-6(j-1)/(n-1)), Haar factors", "parallelism": f"replicas{world}",
+                   "l2": f"inputs larger than L2 (A is {4 * float((ms * ns).sum()) / 2**20:.0f} MiB)",
+                   "variant": variant, "autotune_ms": tune_ms},
+        "tflops": achieved, "flops_per_step": F,
+        "per_matrix_launches": {"ms": per_matrix_ms, "matrices_per_s": count / (per_matrix_ms * 1e-3),
+                                "note": "same device code, one launch per matrix, one stream; timed on every "
+                                        "16th matrix (largest first) and scaled by its share of the m n^2 work"},
+        "speedup_vs_per_matrix_launches": per_matrix_ms / ms_step,
+        "no_graph_ms_per_step": nograph_ms,
+        "errors": {"recon_rel_fro_max_sample": worst_rec, "sample": "every 64th matrix"},
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": count * world / (e2e_ms * 1e-3), "unit": "matrices/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": 4 * b.A.numel(),
+                "d2h_bytes_per_step": 4 * (b.U.numel() + b.R.numel() + b.V.numel()), "steps": e2e_steps},
+        "gpu_launches": launches, "clocks": csum,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _batched_cpu(mats, ms, ns, q, reorth, budget_s: float = 15.0):
+    """The FP64 oracle on the batch's matrices in order until ~budget_s of CPU time: matrices/s."""
+    import numpy as np
+    import oracle
+    from paper_1812_06007_gb300 import workloads as W
+    oracle.build()
+    done, t0 = 0, time.perf_counter()
+    for i, X in enumerate(mats):
+        oracle.urv(np.asarray(X, dtype=np.float64), q, reorth, W.batched_seed(i))
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t = time.perf_counter() - t0
+    frac = float((ms[:done] * ns[:done] ** 2).sum() / (ms * ns ** 2).sum())
+    # scale to the whole batch by its share of m n^2 work: matrices/s of the full mix
+    return {"value": len(mats) / (t / max(frac, 1e-12)), "unit": "matrices/s",
+            "cores": int(os.environ.get("OMP_NUM_THREADS", 0)) or os.cpu_count(), "kind": "oracle",
+            "sample": f"first {done} matrices of the batch ({100 * frac:.1f}% of its m n^2 work) in {t:.1f} s, "
+                      "FP64 C oracle (OpenMP), scaled to the full batch by work share"}
+
+
+def run_batched_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1812_06007_gb300 import workloads as W
+    ms, ns = W.batched_shapes(a.count)
+    mats = [W.batched_matrix_np(int(ms[i]), int(ns[i]), i) for i in range(min(a.count, 400))]
+    vals = []
+    cpu = None
+    for _ in range(a.warmup + a.steps):
+        cpu = _batched_cpu(mats, ms[:len(mats)], ns[:len(mats)], a.q, a.reorth, budget_s=10.0)
+        vals.append(cpu["value"])
+    vals = vals[a.warmup:]
+    value = statistics.median(vals)
+    cpu["value"] = value
+    line = {"impl": "reference", "metric": BATCHED_METRIC, "value": value, "unit": "matrices/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": a.count / value * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"batched PowerURV, {a.count} matrices, q={a.q}",
+                                            "l2": "n/a (CPU)"},
+            "cpu_baseline": cpu, "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- adjoint -----
+ADJOINT_METRIC = "PowerURV adjoint (FP64 reverse mode, G fixed) seconds per backward, m=n=2048 q=2 reorth"
+
+
+def adjoint_flops(m, n, q, reorth):
+    """Flops of the reverse call: the recomputed forward pass plus, per QR, its reverse rule
+    (two n x n x m products, one m x n x n product, the triangular inverse n^3/3 and
+    X R^-T, m n^2) and per power product two transposed products."""
+    fwd = urv_flops(m, n, q, reorth)
+    nqr_m = (q if reorth else 0) + 1
+    nqr_n = (q - 1 if (reorth and q > 0) else 0) + 1
+    qrb = lambda r: 2 * (2.0 * n * n * r) + 2.0 * r * n * n + n ** 3 / 3.0 + 2.0 * r * n * n
+    return fwd + nqr_m * qrb(m) + nqr_n * qrb(n) + 2 * q * 2 * (2.0 * m * n * n) + 2 * (2.0 * m * n * n)
+
+
+def run_adjoint(a):
+    import numpy as np
+    import torch
+    from paper_1812_06007_gb300 import binding as B
+    from paper_1812_06007_gb300 import build as Bld
+    from paper_1812_06007_gb300 import workloads as W
+    Bld.build()
+    B.lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = a.n if a.n != 16384 else 2048
+    m, q, reorth = (a.m if a.m != a.n else n), a.q, a.reorth
+    A = W.gaussian_matrix_torch(m, n, 2048, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.SEED_B)
+    Ub = torch.randn(n, m, generator=gen, device=dev, dtype=torch.float64).t()
+    Rb = torch.randn(n, n, generator=gen, device=dev, dtype=torch.float64).t()
+    Vb = torch.randn(n, n, generator=gen, device=dev, dtype=torch.float64).t()
+    ws = torch.empty(B.purl_urv_backward_workspace_bytes(m, n, q), dtype=torch.uint8, device=dev)
+    Ab = B.empty_colmajor(m, n, dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        B.purl_urv_backward(A, q, reorth, W.SEED_G, Ub, Rb, Vb, out=Ab, workspace=ws, stream=stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    B.purl_profile_reset()
+    B.purl_profile_enable(True)
+    launches0 = B.purl_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        e0.record(stream)
+        for _ in range(a.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = B.purl_launch_count() - launches0
+    named = B.purl_profile_read_named()
+    B.purl_profile_enable(False)
+    sec = e0.elapsed_time(e1) / a.steps * 1e-3
+    F = adjoint_flops(m, n, q, reorth)
+    roof = roofline(None, named, a.steps, "fp64")
+    # end to end: A and cotangents from pinned host memory, gradient back
+    hA, hU = A.cpu().pin_memory(), Ub.cpu().pin_memory()
+    hR, hV, hAb = Rb.cpu().pin_memory(), Vb.cpu().pin_memory(), torch.empty_like(Ab.cpu()).pin_memory()
+    dA, dU, dR, dV = (B.empty_colmajor(*t.shape, dev) for t in (A, Ub, Rb, Vb))
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    for _ in range(max(1, min(a.steps, 3))):
+        for d_, h_ in ((dA, hA), (dU, hU), (dR, hR), (dV, hV)):
+            d_.copy_(h_, non_blocking=True)
+        B.purl_urv_backward(dA, q, reorth, W.SEED_G, dU, dR, dV, out=Ab, workspace=ws, stream=stream)
+        hAb.copy_(Ab, non_blocking=True)
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_sec = x0.elapsed_time(x1) / max(1, min(a.steps, 3)) * 1e-3
+    cpu = None
+    if not a.no_cpu_baseline:
+        cpu = _adjoint_cpu(n, q, reorth)
+    line = {
+        "metric": ADJOINT_METRIC, "value": sec, "unit": "s", "n_gpus": 1, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"PowerURV reverse mode m={m} n={n} q={q} reorth={int(reorth)}, Gaussian A, "
+                               "random cotangents", "m": m, "n": n, "q": q, "reorth": reorth,
+                   "l2": f"working set {8 * (6 * m * n + 12 * n * n) / 2**20:.0f} MiB > L2"},
+        "tflops": F / sec / 1e12, "flops_per_step": F, "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_sec, "unit": "s", "h2d_bytes_per_step": 8 * (2 * m * n + 2 * n * n),
+                "d2h_bytes_per_step": 8 * m * n},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "kernels_by_name": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / a.steps}
+                            for k, v in sorted(named.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _adjoint_cpu(n_full, q, reorth, n_sample: int = 384):
+    """The oracle's reverse mode on an n_sample square Gaussian matrix, scaled to n_full by n^3."""
+    import numpy as np
+    from oracle import adjoint as oadj
+    from paper_1812_06007_gb300 import workloads as W
+    A = W.gaussian_matrix_np(n_sample, n_sample, 2048)
+    rng = np.random.default_rng(W.SEED_B)
+    Ub, Rb, Vb = (rng.standard_normal((n_sample, n_sample)) for _ in range(3))
+    t0 = time.perf_counter()
+    oadj.urv_backward(A, q, reorth, W.SEED_G, Ub, Rb, Vb)
+    t = time.perf_counter() - t0
+    scale = (n_full / n_sample) ** 3
+    return {"value": t * scale, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle reverse mode at m=n={n_sample} ({t:.2f} s; C QR + numpy products), "
+                      f"scaled by (n/{n_sample})^3 to n={n_full}"}
+
+
+def run_adjoint_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = a.n if a.n != 16384 else 2048
+    vals = []
+    cpu = None
+    for _ in range(a.warmup + a.steps):
+        cpu = _adjoint_cpu(n, a.q, a.reorth)
+        vals.append(cpu["value"])
+    value = statistics.median(vals[a.warmup:])
+    cpu["value"] = value
+    line = {"impl": "reference", "metric": ADJOINT_METRIC, "value": value, "unit": "s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"PowerURV reverse mode m=n={n} q={a.q}", "l2": "n/a (CPU)"},
+            "cpu_baseline": cpu, "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = parse()
+    if a.workload == "batched":
+        return run_batched_reference(a) if a.impl == "reference" else run_batched(a)
+    if a.workload == "adjoint":
+        return run_adjoint_reference(a) if a.impl == "reference" else run_adjoint(a)
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)
