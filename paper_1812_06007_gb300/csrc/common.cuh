@@ -64,8 +64,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target,
       unsigned v;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
       if (v >= target) break;
-      if (*(volatile int *)&ctrl->abort) { ok = 0; break; }
-      if (++polls > kSpinLimit) {
+      // the abort flag is a second L2 round trip: look at it every 64 polls
+      if ((++polls & 63) == 0 && *(volatile int *)&ctrl->abort) { ok = 0; break; }
+      if (polls > kSpinLimit) {
         atomicCAS(&ctrl->status, PURL_OK, PURL_ERR_TIMEOUT);
         atomicExch(&ctrl->abort, 1);
         ok = 0;

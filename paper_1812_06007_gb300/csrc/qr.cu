@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
                                                     unsigned *counter, DeviceControl *ctrl) {
   extern __shared__ double Ps[];  // ch x QR_B, column-major (column t at Ps + t*ch)
   __shared__ double s_w[QR_B];
-  __shared__ double s_par[4];     // beta, v0, tau, 1/v0
+  __shared__ double s_par[4];     // beta, -, tau, 1/v0
+  __shared__ double s_red[PW][32];
   const int P = gridDim.x;
   const int c = blockIdx.x;
   const int r0 = c * ch;
@@ -78,32 +79,58 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
       for (int t = k + tid; t < bw; t += PNT) __stcg(&rk[t], Ps[t * ch + (k - r0)]);
     // (b) one barrier per column
     if (!grid_barrier(counter, (unsigned)(k + 1) * P, ctrl)) return;
-    // (c) every block reduces the partials in the same fixed order
-    for (int t = k + warp; t < bw; t += PW) {
-      double s = 0.0;
-      for (int b = lane; b < P; b += 32) s += __ldcg(&pb[(size_t)b * QR_B + t]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) s_w[t] = s;  // s_w[k] = sigma, s_w[t>k] = dot_t
+    // (c) every block reduces the partials in the same fixed order: thread
+    // (t = tid % 32, j = tid / 32) sums blocks j, j + 8, ... with independent
+    // loads (one L2 round trip, not one per block), warp 0 adds the 8 partial
+    // sums and forms the reflector.  Row k is fetched in the same round trip.
+    const double rkt = (warp == 0 && lane < bw) ? __ldcg(&rk[lane]) : 0.0;
+    {
+      const int t = tid & 31, j = tid >> 5;
+      double acc = 0.0;
+      if (t >= k && t < bw) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int b = j;
+        for (; b + 3 * PW < P; b += 4 * PW) {
+          a0 += __ldcg(&pb[(size_t)b * QR_B + t]);
+          a1 += __ldcg(&pb[(size_t)(b + PW) * QR_B + t]);
+          a2 += __ldcg(&pb[(size_t)(b + 2 * PW) * QR_B + t]);
+          a3 += __ldcg(&pb[(size_t)(b + 3 * PW) * QR_B + t]);
+        }
+        for (; b < P; b += PW) a0 += __ldcg(&pb[(size_t)b * QR_B + t]);
+        acc = (a0 + a1) + (a2 + a3);
+      }
+      s_red[j][t] = acc;
     }
     __syncthreads();
-    if (tid == 0) {
-      double sigma = s_w[k];
-      double x0 = __ldcg(&rk[k]);
+    if (warp == 0) {
+      double S = 0.0;
+#pragma unroll
+      for (int j = 0; j < PW; ++j) S += s_red[j][lane];  // s_w-like: S(k) = sigma, S(t>k) = dot_t
+      const double sigma = __shfl_sync(0xffffffffu, S, k);
+      const double x0 = __shfl_sync(0xffffffffu, rkt, k);
+      double beta, tk, inv_v0;
       if (sigma == 0.0) {
-        s_par[0] = x0; s_par[1] = 1.0; s_par[2] = 0.0; s_par[3] = 1.0;
+        beta = x0; tk = 0.0; inv_v0 = 1.0;
       } else {
-        double norm = sqrt(x0 * x0 + sigma);
-        double beta = (x0 >= 0.0) ? -norm : norm;
-        s_par[0] = beta; s_par[1] = x0 - beta; s_par[2] = (beta - x0) / beta; s_par[3] = 1.0 / (x0 - beta);
+        // one division: r = 1 / (v0 norm) gives 1/v0 = norm r and
+        // tau = (beta - x0) / beta = |v0| / norm = |v0| v0 r
+        const double norm = sqrt(fma(x0, x0, sigma));
+        beta = (x0 >= 0.0) ? -norm : norm;
+        const double v0 = x0 - beta;
+        const double r = 1.0 / (v0 * norm);
+        inv_v0 = norm * r;
+        tk = fabs(v0) * v0 * r;
       }
-      if (c == 0) tau[k] = s_par[2];
+      // w_t = tau (a_kt + v(k+1:)^T a_t) with v(k+1:) = x(k+1:)/v0
+      if (lane > k && lane < bw) s_w[lane] = tk * (rkt + S * inv_v0);
+      if (lane == 0) {
+        s_par[0] = beta; s_par[2] = tk; s_par[3] = inv_v0;
+        if (c == 0) tau[k] = tk;
+      }
     }
     __syncthreads();
     const double beta = s_par[0], tk = s_par[2], inv_v0 = s_par[3];
     if (tk != 0.0) {
-      // w_t = tau (a_kt + v(k+1:)^T a_t) with v(k+1:) = x(k+1:)/v0 (one division, then products)
-      for (int t = k + 1 + tid; t < bw; t += PNT) s_w[t] = tk * (__ldcg(&rk[t]) + s_w[t] * inv_v0);
       for (int i = i_lo + tid; i < nr; i += PNT) Ps[k * ch + i] *= inv_v0;
       __syncthreads();
       if (k >= r0 && k < r0 + nr && tid == 0) Ps[k * ch + (k - r0)] = beta;
