@@ -158,26 +158,43 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
 }
 
 // ------------------------------------------------------------ T factor ----
-// Sum the split-K partials of the Gram matrix V^T V and run the forward
-// column recurrence of the compact-WY T factor.  One block.
+// Sum the split-K partials of the Gram matrix V^T V and form the compact-WY T
+// factor (I - V T V^T = H_0 ... H_{b-1}).  One block.  On this GPU a dependent
+// FP64 operation costs tens of cycles, so the column recurrence
+//   T(0:k,k) = -tau_k T(0:k,0:k) G(0:k,k)
+// (a chain of ~b^2/2 dependent FMAs per row) is evaluated blockwise: the
+// recurrence inside diagonal blocks of 8 columns, then the standard merge of
+// two adjacent blocks, T12 = -T11 (G12 T22), on blocks of 8 and 16 columns,
+// all threads working on independent entries.
 // With tau_from_gram, tau_k is re-derived as 2 / (v_k^T v_k) from the Gram
 // matrix itself, so that each I - tau_k v_k v_k^T is orthogonal for exactly the
 // vectors the Gram matrix was formed from (used when the products see a
 // rounded copy of V).
 __global__ void __launch_bounds__(256) larft_kernel(int bw, int splits, const double *Gp,
                                                     const double *tau, double *T, bool tau_from_gram) {
+  constexpr int LF = 8;
   __shared__ double Gm[QR_B][QR_B + 1];
   __shared__ double Ts[QR_B][QR_B + 1];
+  __shared__ double tmp[QR_B * QR_B / 2];
   __shared__ double tks[QR_B];
-  for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) {
-    int i = e % bw, j = e / bw;
-    double s = 0.0;
-    for (int z = 0; z < splits; ++z) s += Gp[(size_t)z * bw * bw + e];
-    Gm[i][j] = s;
+  for (int e = threadIdx.x; e < QR_B * QR_B; e += blockDim.x) {
+    const int i = e % QR_B, j = e / QR_B;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (i < bw && j < bw) {
+      const int f = i + j * bw;
+      int z = 0;
+      for (; z + 3 < splits; z += 4) {
+        a0 += Gp[(size_t)z * bw * bw + f];
+        a1 += Gp[(size_t)(z + 1) * bw * bw + f];
+        a2 += Gp[(size_t)(z + 2) * bw * bw + f];
+        a3 += Gp[(size_t)(z + 3) * bw * bw + f];
+      }
+      for (; z < splits; ++z) a0 += Gp[(size_t)z * bw * bw + f];
+    }
+    Gm[i][j] = (a0 + a1) + (a2 + a3);
     Ts[i][j] = 0.0;
   }
   __syncthreads();
-  // the tau_k, each computed once (an FP64 division is a long sequence)
   if (threadIdx.x < bw) {
     const int k = threadIdx.x;
     double tk = tau[k];
@@ -185,15 +202,48 @@ __global__ void __launch_bounds__(256) larft_kernel(int bw, int splits, const do
     tks[k] = tk;
   }
   __syncthreads();
-  for (int k = 0; k < bw; ++k) {
-    const double tk = tks[k];
-    int i = threadIdx.x;
-    double s = 0.0;
-    if (i < k)
-      for (int l = i; l < k; ++l) s += Ts[i][l] * Gm[l][k];
+  // diagonal blocks: thread i owns row i of its block
+  if (threadIdx.x < bw) {
+    const int i = threadIdx.x, a = (i / LF) * LF;
+    for (int k = i; k < a + LF && k < bw; ++k) {
+      if (k == i) {
+        Ts[i][k] = tks[k];
+      } else {
+        double s0 = 0.0, s1 = 0.0;
+        int l = i;
+        for (; l + 1 < k; l += 2) {
+          s0 = fma(Ts[i][l], Gm[l][k], s0);
+          s1 = fma(Ts[i][l + 1], Gm[l + 1][k], s1);
+        }
+        if (l < k) s0 = fma(Ts[i][l], Gm[l][k], s0);
+        Ts[i][k] = -tks[k] * (s0 + s1);
+      }
+    }
+  }
+  __syncthreads();
+  for (int h = LF; h < QR_B; h *= 2) {
+    const int outs = (QR_B / (2 * h)) * h * h;
+    for (int e = threadIdx.x; e < outs; e += blockDim.x) {  // tmp = G12 T22
+      const int pr = e / (h * h), i = (e % (h * h)) / h, j = e % h;
+      const int a = pr * 2 * h, b0 = a + h;
+      double s0 = 0.0, s1 = 0.0;
+      for (int l = 0; l <= j; l += 2) {
+        s0 = fma(Gm[a + i][b0 + l], Ts[b0 + l][b0 + j], s0);
+        if (l + 1 <= j) s1 = fma(Gm[a + i][b0 + l + 1], Ts[b0 + l + 1][b0 + j], s1);
+      }
+      tmp[e] = s0 + s1;
+    }
     __syncthreads();
-    if (i < k) Ts[i][k] = -tk * s;
-    if (i == k) Ts[k][k] = tk;
+    for (int e = threadIdx.x; e < outs; e += blockDim.x) {  // T12 = -T11 tmp
+      const int pr = e / (h * h), i = (e % (h * h)) / h, j = e % h;
+      const int a = pr * 2 * h, b0 = a + h;
+      double s0 = 0.0, s1 = 0.0;
+      for (int l = i; l < h; l += 2) {
+        s0 = fma(Ts[a + i][a + l], tmp[pr * h * h + l * h + j], s0);
+        if (l + 1 < h) s1 = fma(Ts[a + i][a + l + 1], tmp[pr * h * h + (l + 1) * h + j], s1);
+      }
+      Ts[a + i][b0 + j] = -(s0 + s1);
+    }
     __syncthreads();
   }
   for (int e = threadIdx.x; e < QR_B * QR_B; e += blockDim.x) {
