@@ -76,6 +76,7 @@ def parse():
     ap.add_argument("--no-profile", action="store_true", help="skip per-kernel event timing")
     ap.add_argument("--workload", choices=["urv", "batched", "adjoint"], default="urv")
     ap.add_argument("--count", type=int, default=4096, help="batched: number of matrices")
+    ap.add_argument("--variant", type=int, default=-1, help="batched: kernel variant (-1 = autotune)")
     ap.add_argument("--fp64-n", type=int, default=8192,
                     help="size of the FP64-path comparison run (0 = skip); FP64 at n=16384 takes minutes")
     a = ap.parse_args()
@@ -520,9 +521,12 @@ def run_batched(a):
     host = b.pack_host(mats)
     b.load_packed_a(host)
     stream = torch.cuda.current_stream()
-    variant, tune_ms = b.autotune(q, reorth, stream=stream)
+    if a.variant >= 0:
+        variant, tune_ms = a.variant, None
+    else:
+        variant, tune_ms = b.autotune(q, reorth, stream=stream)
     for _ in range(a.warmup):
-        b.factor(q, reorth, stream=stream)
+        b.factor(q, reorth, variant=variant, stream=stream)
     torch.cuda.synchronize()
     if b.status() != 0:
         raise RuntimeError("batched status not ok after warm-up")
@@ -531,10 +535,10 @@ def run_batched(a):
     gs.wait_stream(stream)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.stream(gs):
-        b.factor(q, reorth, stream=gs)
+        b.factor(q, reorth, variant=variant, stream=gs)
         torch.cuda.synchronize()
         with torch.cuda.graph(g, stream=gs):
-            b.factor(q, reorth, stream=gs)
+            b.factor(q, reorth, variant=variant, stream=gs)
     torch.cuda.synchronize()
     launches0 = B.purl_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -572,7 +576,7 @@ def run_batched(a):
     u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     u0.record(stream)
     for _ in range(a.steps):
-        b.factor(q, reorth, stream=stream)
+        b.factor(q, reorth, variant=variant, stream=stream)
     u1.record(stream)
     torch.cuda.synchronize()
     nograph_ms = u0.elapsed_time(u1) / a.steps
@@ -586,7 +590,7 @@ def run_batched(a):
     e2e_steps = max(1, min(a.steps, 3))
     for _ in range(e2e_steps):
         b.A.copy_(hA, non_blocking=True)
-        b.factor(q, reorth, stream=stream)
+        b.factor(q, reorth, variant=variant, stream=stream)
         hU.copy_(b.U, non_blocking=True)
         hR.copy_(b.R, non_blocking=True)
         hV.copy_(b.V, non_blocking=True)
