@@ -95,6 +95,22 @@ int purl_urv_factor_ex(int m, int n, const double *A, int lda, int q, int reorth
 size_t purl_urv_workspace_bytes(int m, int n, int mode);
 
 /*
+ * purl_ulv_factor_ex -- the wide case m <= n (Section 1: a URV factorization of
+ * A^T gives a ULV factorization of A).  A = U L V^T with U m x m orthogonal,
+ * L m x m lower triangular with a nonnegative diagonal, V n x m with
+ * orthonormal columns, computed as the PowerURV of A^T (n x m) with the same
+ * q, reorth, seed (G is m x m) and mode: A^T = U' R' V'^T gives U = V',
+ * L = R'^T, V = U'.  A is not modified.  Workspace as for purl_urv_factor_ex
+ * (purl_ulv_workspace_bytes; NULL = allocate on `stream`).  Errors: -i for bad
+ * argument i (U = 8, ldu = 9, L = 10, ldl = 11, V = 12, ldv = 13, mode = 14),
+ * PURL_ERR_SHAPE for m > n.
+ */
+int purl_ulv_factor_ex(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                       double *U, int ldu, double *L, int ldl, double *V, int ldv, int mode,
+                       void *workspace, size_t workspace_bytes, cudaStream_t stream);
+size_t purl_ulv_workspace_bytes(int m, int n, int mode);
+
+/*
  * purl_urv_backward -- reverse mode of the FP64 map A -> (U, R, V) of
  * purl_urv_factor (Section 3, Eqs. (5)-(6)) with the Gaussian G held fixed:
  * Abar = J^T (Ubar, Rbar, Vbar), the gradient with respect to A of
@@ -200,6 +216,19 @@ int purl_urv_batched_autotune(int count, const purl_batch_item *items, int max_m
  */
 int purl_gaussian_f32(uint64_t seed, uint64_t stream_id, int rows, int cols, float *G, int ldg,
                       cudaStream_t stream);
+
+/*
+ * purl_wait_probe -- exercises the failure detection (the paper has no
+ * counterpart).  Every device-side wait of the library is bounded: when it
+ * gives up it records PURL_ERR_TIMEOUT in the per-device status word read by
+ * purl_device_status, raises an abort flag that ends the other waits of the
+ * same launch, and returns.  The probe launches `blocks` (1..64) cooperative
+ * blocks of 32 threads through the library's grid barrier with `polls` polls
+ * allowed; with missing = 1 the barrier awaits one block more than exists,
+ * so every wait runs out.  Asynchronous on `stream`; read the outcome with
+ * purl_device_status (which also clears it).  Nothing faults or hangs.
+ */
+int purl_wait_probe(int blocks, int missing, long long polls, cudaStream_t stream);
 
 /*
  * purl_gaussian -- the Gaussian matrix G of Section 3 (the paper fixes no

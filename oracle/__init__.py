@@ -16,6 +16,7 @@ Paper map (sections / equations of the paper):
   qr            Section 2.2, unpivoted Householder QR, diag(R) >= 0
   urv / urv_g   Section 3, Eq. (5) and Eq. (6), re-orthonormalisation in the
                 power iteration (Section 3, third paragraph); q = 0 is DDH-URV
+  ulv           Section 1, the wide case: the URV of A^T read as A = U L V^T
   truncate      Section 5, A_k = U(:,1:k) R(1:k,:) V^T
   jacobi_svd    brute-force singular values for tiny inputs (tests only)
 """
@@ -166,6 +167,20 @@ def urv(A, q: int, reorth: bool, seed: int):
     if rc != 0:
         raise ValueError(f"orc_urv_factor failed ({rc})")
     return U, R, V
+
+
+def ulv(A, q: int, reorth: bool, seed: int):
+    """Wide A (m <= n): (U, L, V) with A = U L V^T, L lower triangular (m x m).
+
+    Section 1: a URV factorization of A^T gives a ULV factorization of A.
+    With A^T = U' R' V'^T (PowerURV of the n x m matrix A^T, G m x m from
+    `seed`): U = V', L = R'^T, V = U'."""
+    A = _f64(A)
+    m, n = A.shape
+    if m > n:
+        raise ValueError("ulv needs m <= n")
+    Up, Rp, Vp = urv(np.asfortranarray(A.T), q, reorth, seed)
+    return np.asfortranarray(Vp), np.asfortranarray(Rp.T), np.asfortranarray(Up)
 
 
 def truncate(U, R, V, k: int) -> np.ndarray:

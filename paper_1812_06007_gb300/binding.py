@@ -35,6 +35,8 @@ SIGNATURES = {
     "purl_urv_factor": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _p]),
     "purl_urv_factor_ex": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
     "purl_urv_workspace_bytes": (_sz, [_i, _i, _i]),
+    "purl_ulv_factor_ex": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
+    "purl_ulv_workspace_bytes": (_sz, [_i, _i, _i]),
     "purl_urv_backward": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _p, _i, _p, _sz, _p]),
     "purl_urv_backward_workspace_bytes": (_sz, [_i, _i, _i]),
     "purl_urv_batched_variants": (_i, []),
@@ -53,6 +55,7 @@ SIGNATURES = {
     "purl_urv_truncate": (_i, [_i, _i, _i, _p, _i, _p, _i, _p, _i, _p, _i, _p]),
     "purl_urv_reconstruct": (_i, [_i, _i, _p, _i, _p, _i, _p, _i, _p, _i, _p]),
     "purl_device_status": (_i, [_p]),
+    "purl_wait_probe": (_i, [_i, _i, ctypes.c_longlong, _p]),
     "purl_launch_count": (ctypes.c_ulonglong, []),
     "purl_profile_enable": (None, [_i]),
     "purl_profile_reset": (None, []),
@@ -173,6 +176,24 @@ def purl_urv_factor(A, q: int, reorth: bool, seed: int, mode: int = PURL_MODE_FP
                                   _ld(R), _ptr(V), _ld(V), mode, ws_ptr, ws_bytes, _stream(stream))
     _check("purl_urv_factor_ex", st)
     return U, R, V
+
+
+def purl_ulv_factor_ex(A, q: int, reorth: bool, seed: int, mode: int = PURL_MODE_FP64, workspace=None,
+                       stream=None):
+    """(U, L, V) with A = U L V^T for a wide A (m <= n), L lower triangular m x m."""
+    _cuda_check(A)
+    m, n = A.shape
+    U, L, V = empty_colmajor(m, m, A.device), empty_colmajor(m, m, A.device), empty_colmajor(n, m, A.device)
+    ws_ptr, ws_bytes = (_ptr(workspace), workspace.numel() * workspace.element_size()) if workspace is not None \
+        else (ctypes.c_void_p(0), 0)
+    st = lib().purl_ulv_factor_ex(m, n, _ptr(A), _ld(A), q, int(bool(reorth)), seed, _ptr(U), _ld(U), _ptr(L),
+                                  _ld(L), _ptr(V), _ld(V), mode, ws_ptr, ws_bytes, _stream(stream))
+    _check("purl_ulv_factor_ex", st)
+    return U, L, V
+
+
+def purl_ulv_workspace_bytes(m: int, n: int, mode: int = PURL_MODE_FP64) -> int:
+    return int(lib().purl_ulv_workspace_bytes(m, n, mode))
 
 
 def purl_urv_workspace_bytes(m: int, n: int, mode: int = PURL_MODE_FP64) -> int:
@@ -331,6 +352,10 @@ def purl_urv_reconstruct(U, R, V, out=None, stream=None):
                                     _ld(Ak), _stream(stream))
     _check("purl_urv_reconstruct", st)
     return Ak
+
+
+def purl_wait_probe(blocks: int, missing: bool, polls: int, stream=None):
+    _check("purl_wait_probe", lib().purl_wait_probe(blocks, int(bool(missing)), polls, _stream(stream)))
 
 
 def purl_device_status(stream=None) -> int:

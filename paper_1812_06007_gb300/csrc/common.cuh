@@ -52,7 +52,7 @@ constexpr long long kSpinLimit = 1LL << 23;
 // on expiry the block records PURL_ERR_TIMEOUT, raises the abort flag and
 // returns false; callers then leave the kernel.
 __device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target,
-                                             DeviceControl *ctrl) {
+                                             DeviceControl *ctrl, long long spin_limit = kSpinLimit) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
@@ -66,7 +66,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target,
       if (v >= target) break;
       // the abort flag is a second L2 round trip: look at it every 64 polls
       if ((++polls & 63) == 0 && *(volatile int *)&ctrl->abort) { ok = 0; break; }
-      if (polls > kSpinLimit) {
+      if (polls > spin_limit) {
         atomicCAS(&ctrl->status, PURL_OK, PURL_ERR_TIMEOUT);
         atomicExch(&ctrl->abort, 1);
         ok = 0;

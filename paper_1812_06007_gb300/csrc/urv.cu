@@ -277,6 +277,57 @@ int purl_urv_factor(int m, int n, const double *A, int lda, int q, int reorth, u
                             nullptr, 0, stream);
 }
 
+// ULV of a wide matrix through the URV of its transpose (Section 1): with
+// A^T = U' R' V'^T (n x m, n >= m), A = V' R'^T U'^T, i.e. U = V' (m x m),
+// L = R'^T (m x m, lower triangular, nonnegative diagonal), V = U' (n x m).
+static int ulv_plan(Arena &ar, int m, int n, int mode, double **At, double **Rt, UrvWork *w) {
+  *At = ar.take<double>((size_t)(n > 0 ? n : 1) * (size_t)(m > 0 ? m : 1));
+  *Rt = ar.take<double>((size_t)(m > 0 ? m : 1) * (size_t)(m > 0 ? m : 1));
+  return urv_plan(ar, n, m, mode, w);
+}
+
+size_t purl_ulv_workspace_bytes(int m, int n, int mode) {
+  if (m < 0 || n < 0 || m > n || !mode_ok(mode)) return 0;
+  Arena ar;
+  double *At, *Rt;
+  UrvWork w;
+  if (ulv_plan(ar, m, n, mode, &At, &Rt, &w) != PURL_OK) return 0;
+  return ar.used;
+}
+
+int purl_ulv_factor_ex(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                       double *U, int ldu, double *L, int ldl, double *V, int ldv, int mode,
+                       void *workspace, size_t workspace_bytes, cudaStream_t stream) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (m > n) return PURL_ERR_SHAPE;
+  if (!A && (long long)m * n > 0) return -3;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  if (q < 0) return -5;
+  if (!U && m > 0) return -8;
+  if (ldu < (m > 1 ? m : 1)) return -9;
+  if (!L && m > 0) return -10;
+  if (ldl < (m > 1 ? m : 1)) return -11;
+  if (!V && (long long)m * n > 0) return -12;
+  if (ldv < (n > 1 ? n : 1)) return -13;
+  if (!mode_ok(mode)) return -14;
+  if (m == 0) return PURL_OK;
+  if (!device_info()) return PURL_ERR_CUDA;
+  const size_t need = purl_ulv_workspace_bytes(m, n, mode);
+  Scratch scratch;
+  PURL_TRY(scratch.acquire(workspace, workspace_bytes, need, stream));
+  Arena ar;
+  ar.base = static_cast<char *>(scratch.ptr);
+  ar.size = workspace ? workspace_bytes : need;
+  double *At, *Rt;
+  UrvWork w;
+  PURL_TRY(ulv_plan(ar, m, n, mode, &At, &Rt, &w));
+  if (!ar.ok) return PURL_ERR_NOMEM;
+  PURL_TRY(transpose_f64(m, n, A, lda, At, n, stream));                                   // A^T, n x m
+  PURL_TRY(urv_run(n, m, At, n, q, reorth, seed, V, ldv, Rt, m, U, ldu, mode, w, stream));  // A^T = V R' U^T
+  return transpose_f64(m, m, Rt, m, L, ldl, stream);                                       // L = R'^T
+}
+
 int purl_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double *G, int ldg,
                   cudaStream_t stream) {
   if (rows < 0) return -3;

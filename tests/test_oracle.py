@@ -324,3 +324,31 @@ def test_golden_fixture_reproduces(tmp_path):
         ref = load_fixture(os.path.join(here, name + ".txt"))
         for key in ref:
             assert np.allclose(got[key], ref[key], rtol=1e-12, atol=1e-14), (name, key)
+
+
+# ------------------------------------------------------------ ULV (m < n) --
+@pytest.mark.parametrize("m,n,q,reorth", [(7, 12, 1, True), (20, 31, 2, True), (16, 16, 0, True), (9, 30, 2, False)])
+def test_ulv_invariants(m, n, q, reorth):
+    # Section 1: the wide case through A^T.  Pinned by what a ULV must satisfy,
+    # not by re-deriving it: A = U L V^T, L lower triangular with diag >= 0,
+    # orthonormal U and V, ||L||_F = ||A||_F, and the interlacing bounds of a
+    # triangular factor against the singular values of A (numpy's SVD).
+    rng = np.random.default_rng(m * 100 + n)
+    A = rng.standard_normal((m, n))
+    U, L, V = oracle.ulv(A, q, reorth, 7)
+    assert U.shape == (m, m) and L.shape == (m, m) and V.shape == (n, m)
+    eps = np.finfo(float).eps
+    assert np.linalg.norm(A - U @ L @ V.T) <= 50 * n * eps * np.linalg.norm(A)
+    assert np.linalg.norm(np.eye(m) - U.T @ U) <= 50 * n * eps
+    assert np.linalg.norm(np.eye(m) - V.T @ V) <= 50 * n * eps
+    assert np.all(np.triu(L, 1) == 0.0) and np.all(np.diag(L) >= 0.0)
+    assert abs(np.linalg.norm(L) - np.linalg.norm(A)) <= 1e-12 * np.linalg.norm(A)
+    s = np.linalg.svd(A, compute_uv=False)
+    for k in range(1, m):
+        assert np.linalg.svd(L[:k, :k], compute_uv=False)[-1] <= s[k - 1] * (1 + 1e-12)
+        assert np.linalg.norm(L[k:, k:], 2) >= s[k] * (1 - 1e-12)
+
+
+def test_ulv_rejects_tall():
+    with pytest.raises(ValueError):
+        oracle.ulv(np.zeros((5, 3)), 1, True, 7)
