@@ -111,6 +111,27 @@ int purl_ulv_factor_ex(int m, int n, const double *A, int lda, int q, int reorth
 size_t purl_ulv_workspace_bytes(int m, int n, int mode);
 
 /*
+ * purl_rsvd -- the randomized SVD of Section 6 (Eqs. (rsvd1)-(rsvd4)) in FP64,
+ * started from the first l columns of PowerURV's Gaussian draw for `seed`
+ * (the G_rsvd = G(:, 1:l) of the paper's Lemma, so range(U) equals the
+ * range of the first l columns of purl_urv_factor's U for the same seed).
+ *   Y = A (A^T A)^q G_rsvd (re-orthonormalised after every product when
+ *   `reorth`), Y = Q R, Q^T A = W Sigma V^T, U = Q W.
+ *   m, n, A, lda     input (not modified);  1 <= l <= min(m, n, 512).
+ *   U (m x l, ldu), S (l, decreasing), V (n x l, ldv): outputs; each pair
+ *   (U(:,j), V(:,j)) is signed so that U's entry of largest magnitude is
+ *   positive.
+ * The small SVD is a one-sided Jacobi iteration on an l x l factor in one
+ * thread block (bounded number of sweeps).  Workspace as for
+ * purl_urv_factor_ex (purl_rsvd_workspace_bytes).  Errors: -i for bad
+ * argument i, PURL_ERR_NOMEM, PURL_ERR_CUDA.
+ */
+int purl_rsvd(int m, int n, const double *A, int lda, int l, int q, int reorth, uint64_t seed,
+              double *U, int ldu, double *S, double *V, int ldv, void *workspace,
+              size_t workspace_bytes, cudaStream_t stream);
+size_t purl_rsvd_workspace_bytes(int m, int n, int l);
+
+/*
  * purl_urv_backward -- reverse mode of the FP64 map A -> (U, R, V) of
  * purl_urv_factor (Section 3, Eqs. (5)-(6)) with the Gaussian G held fixed:
  * Abar = J^T (Ubar, Rbar, Vbar), the gradient with respect to A of

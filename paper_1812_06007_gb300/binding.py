@@ -37,6 +37,8 @@ SIGNATURES = {
     "purl_urv_workspace_bytes": (_sz, [_i, _i, _i]),
     "purl_ulv_factor_ex": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
     "purl_ulv_workspace_bytes": (_sz, [_i, _i, _i]),
+    "purl_rsvd": (_i, [_i, _i, _p, _i, _i, _i, _i, _u64, _p, _i, _p, _p, _i, _p, _sz, _p]),
+    "purl_rsvd_workspace_bytes": (_sz, [_i, _i, _i]),
     "purl_urv_backward": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _p, _i, _p, _sz, _p]),
     "purl_urv_backward_workspace_bytes": (_sz, [_i, _i, _i]),
     "purl_urv_batched_variants": (_i, []),
@@ -190,6 +192,25 @@ def purl_ulv_factor_ex(A, q: int, reorth: bool, seed: int, mode: int = PURL_MODE
                                   _ld(L), _ptr(V), _ld(V), mode, ws_ptr, ws_bytes, _stream(stream))
     _check("purl_ulv_factor_ex", st)
     return U, L, V
+
+
+def purl_rsvd(A, l: int, q: int, seed: int, reorth: bool = False, workspace=None, stream=None):
+    """(U, S, V): randomized SVD A ~ U diag(S) V^T of rank l (FP64)."""
+    torch = _torch()
+    _cuda_check(A)
+    m, n = A.shape
+    U, V = empty_colmajor(m, l, A.device), empty_colmajor(n, l, A.device)
+    S = torch.empty(l, dtype=torch.float64, device=A.device)
+    ws_ptr, ws_bytes = (_ptr(workspace), workspace.numel() * workspace.element_size()) if workspace is not None \
+        else (ctypes.c_void_p(0), 0)
+    st = lib().purl_rsvd(m, n, _ptr(A), _ld(A), l, q, int(bool(reorth)), seed, _ptr(U), _ld(U), _ptr(S), _ptr(V),
+                         _ld(V), ws_ptr, ws_bytes, _stream(stream))
+    _check("purl_rsvd", st)
+    return U, S, V
+
+
+def purl_rsvd_workspace_bytes(m: int, n: int, l: int) -> int:
+    return int(lib().purl_rsvd_workspace_bytes(m, n, l))
 
 
 def purl_ulv_workspace_bytes(m: int, n: int, mode: int = PURL_MODE_FP64) -> int:

@@ -75,6 +75,8 @@ def test_argument_errors_are_reported_before_device_work(purl):
     assert L.purl_ulv_factor_ex(5, 3, fake, 5, 1, 1, 7, fake, 5, fake, 5, fake, 3, 0, nul, 0, nul) == \
         purl.PURL_ERR_SHAPE
     assert L.purl_ulv_factor_ex(3, 5, fake, 2, 1, 1, 7, fake, 3, fake, 3, fake, 5, 0, nul, 0, nul) == -4
+    assert L.purl_rsvd(10, 8, fake, 10, 9, 1, 0, 7, fake, 10, fake, fake, 8, nul, 0, nul) == -5
+    assert L.purl_rsvd(10, 8, fake, 10, 4, -1, 0, 7, fake, 10, fake, fake, 8, nul, 0, nul) == -6
     # empty problems are valid no-ops
     assert L.purl_urv_factor(0, 0, nul, 1, 1, 1, 7, nul, 1, nul, 1, nul, 1, nul) == 0
     assert L.purl_urv_factor(5, 0, nul, 5, 1, 1, 7, nul, 5, nul, 1, nul, 1, nul) == 0
