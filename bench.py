@@ -74,7 +74,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip per-kernel event timing")
-    ap.add_argument("--workload", choices=["urv", "batched", "adjoint"], default="urv")
+    ap.add_argument("--workload", choices=["urv", "batched", "adjoint", "rsvd"], default="urv")
+    ap.add_argument("--rank", type=int, default=256, help="rsvd: target rank l")
     ap.add_argument("--count", type=int, default=4096, help="batched: number of matrices")
     ap.add_argument("--variant", type=int, default=-1, help="batched: kernel variant (-1 = autotune)")
     ap.add_argument("--fp64-n", type=int, default=8192,
@@ -829,12 +830,135 @@ def run_adjoint_reference(a):
     return 0
 
 
+# ---------------------------------------------------------------- rsvd -----
+RSVD_METRIC = "randomized SVD (Section 6) seconds and TFLOP/s, FP64, m=n=8192, l=256, q=2 reorth"
+
+
+def rsvd_flops(m, n, l, q, reorth):
+    """Products 2 m n l per application of A or A^T ((2q + 2) of them), the
+    Householder QRs with explicit Q (2 (2 r l^2 - 2 l^3 / 3) each: q of m x l and
+    q of n x l when re-orthonormalised, one of m x l and one of n x l always),
+    and the two final l x l products; the Jacobi sweeps are not counted."""
+    qr = lambda r: 2.0 * (2.0 * r * l * l - 2.0 * l ** 3 / 3.0)
+    f = (2 * q + 2) * 2.0 * m * n * l + qr(m) + qr(n) + 2.0 * (m + n) * l * l
+    if reorth:
+        f += q * (qr(m) + qr(n))
+    return f
+
+
+def run_rsvd(a):
+    import torch
+    from paper_1812_06007_gb300 import binding as B
+    from paper_1812_06007_gb300 import build as Bld
+    from paper_1812_06007_gb300 import workloads as W
+    Bld.build()
+    B.lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = a.n if a.n != 16384 else 8192
+    m = a.m if a.m != a.n else n
+    l, q, reorth = a.rank, a.q, a.reorth
+    A = W.test_matrix_torch(m, n, W.sigma_profile("exponential", n, decades=6), device=dev)
+    ws = torch.empty(B.purl_rsvd_workspace_bytes(m, n, l), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        U, S, V = B.purl_rsvd(A, l, q, W.SEED_G, reorth, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+    B.purl_profile_reset()
+    B.purl_profile_enable(True)
+    launches0 = B.purl_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        e0.record(stream)
+        for _ in range(a.steps):
+            U, S, V = B.purl_rsvd(A, l, q, W.SEED_G, reorth, workspace=ws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = B.purl_launch_count() - launches0
+    named = B.purl_profile_read_named()
+    B.purl_profile_enable(False)
+    sec = e0.elapsed_time(e1) / a.steps * 1e-3
+    F = rsvd_flops(m, n, l, q, reorth)
+    roof = roofline(None, named, a.steps, "fp64")
+    # accuracy against the exact spectrum of the synthetic matrix (sigma_j prescribed)
+    sig = torch.as_tensor(W.sigma_profile("exponential", n, decades=6)[:l], device=dev)
+    sv_err = float(((S - sig).abs() / sig[0]).max())
+    hA = A.cpu().pin_memory()
+    dA = B.empty_colmajor(m, n, dev)
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    dA.copy_(hA, non_blocking=True)
+    U, S, V = B.purl_rsvd(dA, l, q, W.SEED_G, reorth, workspace=ws, stream=stream)
+    hU, hS, hV = U.cpu(), S.cpu(), V.cpu()
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_sec = x0.elapsed_time(x1) * 1e-3
+    cpu = None
+    if not a.no_cpu_baseline:
+        cpu = _rsvd_cpu(m, n, l, q, reorth)
+    line = {
+        "metric": RSVD_METRIC, "value": sec, "unit": "s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"randomized SVD m={m} n={n} l={l} q={q} reorth={int(reorth)}, "
+                               "sigma 10^(-6(j-1)/(n-1)), Haar-like factors", "m": m, "n": n, "l": l, "q": q,
+                   "reorth": reorth, "l2": f"inputs larger than L2 (A is {8 * m * n / 2**20:.0f} MiB)"},
+        "tflops": F / sec / 1e12, "flops_per_step": F,
+        "errors": {"max_abs_sigma_err_rel_sigma1": sv_err},
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_sec, "unit": "s", "h2d_bytes_per_step": 8 * m * n,
+                "d2h_bytes_per_step": 8 * (m * l + l + n * l)},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "kernels_by_name": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / a.steps}
+                            for k, v in sorted(named.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _rsvd_cpu(m_full, n_full, l_full, q, reorth, n_sample: int = 768):
+    """The oracle's RSVD on a scaled-down problem (m = n = n_sample, l scaled), scaled by m n l."""
+    from oracle import rsvd as orsvd
+    from paper_1812_06007_gb300 import workloads as W
+    ls = max(1, int(round(l_full * n_sample / n_full)))
+    A = W.test_matrix_np(n_sample, n_sample, W.sigma_profile("exponential", n_sample, decades=6))
+    t0 = time.perf_counter()
+    orsvd.rsvd(A, ls, q, W.SEED_G, reorth)
+    t = time.perf_counter() - t0
+    scale = (m_full * n_full * l_full) / (n_sample * n_sample * ls)
+    return {"value": t * scale, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle RSVD at m=n={n_sample}, l={ls} ({t:.2f} s; C QR + numpy products and SVD), "
+                      f"scaled by m n l to the full problem"}
+
+
+def run_rsvd_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = a.n if a.n != 16384 else 8192
+    vals, cpu = [], None
+    for _ in range(a.warmup + a.steps):
+        cpu = _rsvd_cpu(n, n, a.rank, a.q, a.reorth)
+        vals.append(cpu["value"])
+    value = statistics.median(vals[a.warmup:])
+    cpu["value"] = value
+    line = {"impl": "reference", "metric": RSVD_METRIC, "value": value, "unit": "s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"randomized SVD m=n={n} l={a.rank} q={a.q}", "l2": "n/a (CPU)"},
+            "cpu_baseline": cpu, "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     if a.workload == "batched":
         return run_batched_reference(a) if a.impl == "reference" else run_batched(a)
     if a.workload == "adjoint":
         return run_adjoint_reference(a) if a.impl == "reference" else run_adjoint(a)
+    if a.workload == "rsvd":
+        return run_rsvd_reference(a) if a.impl == "reference" else run_rsvd(a)
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

@@ -8,10 +8,11 @@
 // Singular values are sorted in decreasing order and each pair (U(:,j),
 // V(:,j)) is signed so that U's entry of largest magnitude is positive.
 //
-// The l x l SVD runs in one CTA: Hestenes' one-sided Jacobi method with the
-// round-robin (circle) ordering, so each round rotates l/2 disjoint column
-// pairs in parallel, one pair per warp; sweeps stop when no pair needs a
-// rotation (|a_p . a_q| <= l eps ||a_p|| ||a_q||) or after a fixed number.
+// The l x l SVD is Hestenes' one-sided Jacobi method with the round-robin
+// (circle) ordering: each round rotates l/2 disjoint column pairs in
+// parallel, one pair per thread block of a cooperative grid, with one grid
+// barrier per round; sweeps stop when no pair needs a rotation
+// (|a_p . a_q| <= l eps ||a_p|| ||a_q||) or after a fixed number.
 #include "common.cuh"
 #include "profile.cuh"
 #include "qr.cuh"
@@ -26,7 +27,6 @@ namespace {
 
 constexpr int kMaxL = 512;
 constexpr int kMaxSweeps = 60;
-constexpr int JT = 1024;  // Jacobi threads (32 warps)
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -34,70 +34,86 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// M (l x l, ld l) <- M Vr with orthogonal columns; Vr (l x l) accumulated.
-// On exit sig[j] = ||M(:, j)||, M(:, j) /= sig[j] (the left factor W).
-__global__ void __launch_bounds__(JT) jacobi_svd_kernel(int l, double *M, double *Vr, double *sig, int *sweeps_out) {
-  __shared__ int s_rot;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < l * l; e += JT) Vr[e] = (e % l == e / l) ? 1.0 : 0.0;
+// M (l x l, ld l) <- M Vr with orthogonal columns, Vr (l x l) accumulated;
+// on exit sig[j] = ||M(:, j)|| and M(:, j) /= sig[j] (the left factor W).
+// Cooperative launch, all blocks co-resident: in every round each block
+// rotates its column pair(s) with 256 threads, then one bounded grid barrier;
+// the number of rotations of a sweep is counted in rot[sweep] and read by
+// every block after the sweep's last barrier, so all blocks stop after the
+// same sweep.  counter and rot start at zero.
+__device__ __forceinline__ void block_sum3(double &a, double &b, double &g, double (*red)[3]) {
+  a = warp_sum_d(a);
+  b = warp_sum_d(b);
+  g = warp_sum_d(g);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[warp][0] = a; red[warp][1] = b; red[warp][2] = g; }
+  __syncthreads();
+  a = b = g = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[w][0]; b += red[w][1]; g += red[w][2]; }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) jacobi_coop_kernel(int l, double *M, double *Vr, double *sig, unsigned *counter,
+                                                          unsigned *rot, int *sweeps_out, DeviceControl *ctrl) {
+  __shared__ double red[8][3];
+  const int P = gridDim.x, tid = threadIdx.x;
   const int le = l + (l & 1);  // even count: an odd l gets a dummy column that pairs with nothing
   const double tol = (double)l * 2.220446049250313e-16;
+  for (long long e = blockIdx.x * 256LL + tid; e < (long long)l * l; e += (long long)P * 256)
+    Vr[e] = ((int)(e % l) == (int)(e / l)) ? 1.0 : 0.0;
+  unsigned bar = 1;
+  if (!grid_barrier(counter, bar * (unsigned)P, ctrl)) return;
   int sweep = 0;
-  __syncthreads();
   for (; sweep < kMaxSweeps; ++sweep) {
-    if (tid == 0) s_rot = 0;
-    __syncthreads();
     for (int r = 0; r < le - 1; ++r) {
-      for (int k = warp; k < le / 2; k += JT / 32) {
-        // circle method: position 0 stays, positions 1..le-1 rotate by r
+      for (int k = blockIdx.x; k < le / 2; k += P) {
         const int x = k, y = le - 1 - k;
         const int p = (x == 0) ? 0 : 1 + (x - 1 + r) % (le - 1);
         const int qq = (y == 0) ? 0 : 1 + (y - 1 + r) % (le - 1);
         if (p >= l || qq >= l) continue;
         double *mp = M + (size_t)p * l, *mq = M + (size_t)qq * l;
         double a = 0.0, b = 0.0, g = 0.0;
-        for (int i = lane; i < l; i += 32) {
-          const double u = mp[i], v = mq[i];
+        for (int i = tid; i < l; i += 256) {
+          const double u = __ldcg(&mp[i]), v = __ldcg(&mq[i]);
           a = fma(u, u, a);
           b = fma(v, v, b);
           g = fma(u, v, g);
         }
-        a = warp_sum_d(a);
-        b = warp_sum_d(b);
-        g = warp_sum_d(g);
+        block_sum3(a, b, g, red);
         if (g == 0.0 || fabs(g) <= tol * sqrt(a * b)) continue;
         const double zeta = (b - a) / (2.0 * g);
         const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-        for (int i = lane; i < l; i += 32) {
-          const double u = mp[i], v = mq[i];
-          mp[i] = c * u - s * v;
-          mq[i] = s * u + c * v;
-        }
         double *vp = Vr + (size_t)p * l, *vq = Vr + (size_t)qq * l;
-        for (int i = lane; i < l; i += 32) {
-          const double u = vp[i], v = vq[i];
-          vp[i] = c * u - s * v;
-          vq[i] = s * u + c * v;
+        for (int i = tid; i < l; i += 256) {
+          const double u = __ldcg(&mp[i]), v = __ldcg(&mq[i]);
+          __stcg(&mp[i], c * u - s * v);
+          __stcg(&mq[i], s * u + c * v);
+          const double uu = __ldcg(&vp[i]), vv = __ldcg(&vq[i]);
+          __stcg(&vp[i], c * uu - s * vv);
+          __stcg(&vq[i], s * uu + c * vv);
         }
-        if (lane == 0) s_rot = 1;
+        if (tid == 0) atomicAdd(&rot[sweep], 1u);
       }
-      __syncthreads();
+      if (!grid_barrier(counter, ++bar * (unsigned)P, ctrl)) return;
     }
-    const int rotated = s_rot;
-    __syncthreads();
-    if (!rotated) break;
+    if (__ldcg(&rot[sweep]) == 0u) break;
   }
-  for (int j = warp; j < l; j += JT / 32) {
+  for (int j = blockIdx.x; j < l; j += P) {
     double *mj = M + (size_t)j * l;
-    double a = 0.0;
-    for (int i = lane; i < l; i += 32) a = fma(mj[i], mj[i], a);
-    const double nrm = sqrt(warp_sum_d(a));
-    if (lane == 0) sig[j] = nrm;
+    double a = 0.0, b = 0.0, g = 0.0;
+    for (int i = tid; i < l; i += 256) { const double u = __ldcg(&mj[i]); a = fma(u, u, a); }
+    block_sum3(a, b, g, red);
+    const double nrm = sqrt(a);
+    if (tid == 0) sig[j] = nrm;
     if (nrm > 0.0)
-      for (int i = lane; i < l; i += 32) mj[i] /= nrm;
+      for (int i = tid; i < l; i += 256) mj[i] = __ldcg(&mj[i]) / nrm;
   }
-  if (tid == 0 && sweeps_out) *sweeps_out = sweep;
+  if (blockIdx.x == 0 && tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+__global__ void zero_u32_kernel(unsigned *x, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = 0u;
 }
 
 // Sort sigma decreasingly (ties by index) and permute the columns of W and Vr
@@ -158,6 +174,7 @@ __global__ void __launch_bounds__(256) sign_pairs_kernel(int m, int n, double *U
 struct RsvdPlan {
   double *X, *P, *Q, *Bt, *Q2, *R2, *M, *Vr, *sig, *Ws, *Vs, *F;
   int *sweeps;
+  unsigned *jcount;  // grid-barrier counter, then one rotation count per sweep
   QrWork qw;
 };
 
@@ -176,6 +193,7 @@ int rsvd_plan(Arena &ar, int m, int n, int l, RsvdPlan *p) {
   p->Vs = ar.take<double>(ll);
   p->F = ar.take<double>((size_t)(m > n ? m : n) * l);
   p->sweeps = ar.take<int>(1);
+  p->jcount = ar.take<unsigned>(1 + kMaxSweeps);
   return qr_plan(ar, m > n ? m : n, l, PURL_MODE_FP64, &p->qw);
 }
 
@@ -200,9 +218,22 @@ int rsvd_run(int m, int n, const double *A, int lda, int l, int q, int reorth, u
   PURL_TRY(gemm_f64(true, false, n, l, m, 1.0, A, lda, p.Q, m, 0.0, p.Bt, n, s));    // B^T = A^T Q
   PURL_TRY(qr_into(n, l, p.Bt, n, p.Q2, n, p.R2, l, p, s));                           // B^T = Q2 R2
   PURL_TRY(transpose_f64(l, l, p.R2, l, p.M, l, s));                                  // M = R2^T
-  { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "jacobi_svd_kernel");
-    jacobi_svd_kernel<<<1, JT, 0, s>>>(l, p.M, p.Vr, p.sig, p.sweeps); }            // M = W Sigma Vr^T (rsvd3)
-  PURL_CUDA_TRY(cudaGetLastError());
+  {
+    // M = W Sigma Vr^T (rsvd3): one column pair per block and round
+    const DeviceInfo *di = device_info();
+    const int le = l + (l & 1);
+    int P = le / 2 < di->num_sms ? le / 2 : di->num_sms;
+    if (P < 1) P = 1;
+    { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "zero_u32_kernel");
+      zero_u32_kernel<<<1, 128, 0, s>>>(p.jcount, 1 + kMaxSweeps); }
+    PURL_CUDA_TRY(cudaGetLastError());
+    unsigned *counter = p.jcount, *rot = p.jcount + 1;
+    DeviceControl *ctrl = di->ctrl;
+    int lv = l;
+    void *args[] = {&lv, &p.M, &p.Vr, &p.sig, &counter, &rot, &p.sweeps, &ctrl};
+    LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "jacobi_coop_kernel");
+    PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)jacobi_coop_kernel, dim3(P), dim3(256), args, 0, s));
+  }
   { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "sort_sv_kernel");
     sort_sv_kernel<<<1, 256, 0, s>>>(l, p.sig, p.M, p.Vr, S, p.Ws, p.Vs); }
   PURL_CUDA_TRY(cudaGetLastError());
