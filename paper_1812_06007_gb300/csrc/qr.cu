@@ -37,6 +37,7 @@ namespace {
 
 constexpr int PNT = 256;  // panel kernel threads
 constexpr int PW = PNT / 32;
+constexpr int kPanelMaxBlocks = 160;  // panel grids have at most this many blocks (>= the SM count)
 
 // ------------------------------------------------------------ panel -------
 // F points at F(j0, j0); the panel has `rows` rows and `bw` <= QR_B columns.
@@ -88,16 +89,16 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
       const int t = tid & 31, j = tid >> 5;
       double acc = 0.0;
       if (t >= k && t < bw) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int b = j;
-        for (; b + 3 * PW < P; b += 4 * PW) {
-          a0 += __ldcg(&pb[(size_t)b * QR_B + t]);
-          a1 += __ldcg(&pb[(size_t)(b + PW) * QR_B + t]);
-          a2 += __ldcg(&pb[(size_t)(b + 2 * PW) * QR_B + t]);
-          a3 += __ldcg(&pb[(size_t)(b + 3 * PW) * QR_B + t]);
+        // all of this thread's partials are loaded before any is added, so
+        // the loads share one round trip (P <= kPanelMaxBlocks)
+        double v[kPanelMaxBlocks / PW];
+#pragma unroll
+        for (int u = 0; u < kPanelMaxBlocks / PW; ++u) {
+          const int b = j + u * PW;
+          v[u] = (b < P) ? __ldcg(&pb[(size_t)b * QR_B + t]) : 0.0;
         }
-        for (; b < P; b += PW) a0 += __ldcg(&pb[(size_t)b * QR_B + t]);
-        acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+        for (int u = 0; u < kPanelMaxBlocks / PW; ++u) acc += v[u];
       }
       s_red[j][t] = acc;
     }
@@ -386,6 +387,7 @@ int panel_capacity(const DeviceInfo *di, size_t smem) {
 int panel_blocks(int rows, const DeviceInfo *di) {
   int P = ceil_div(rows, 64);
   if (P > di->num_sms) P = di->num_sms;
+  if (P > kPanelMaxBlocks) P = kPanelMaxBlocks;
   return P < 1 ? 1 : P;
 }
 
