@@ -33,6 +33,10 @@ namespace {
 constexpr int BT = 256;  // threads per CTA
 constexpr int GBK = 16, GPAD = 4;
 constexpr int kMaxM = 1024, kMaxN = 512;
+constexpr int RC = 256;  // rows of V staged at a time by the rank-NB updates
+
+// Row stride (floats) of W staged for a rank update with N columns.
+__host__ __device__ inline int rank_ws_ld(int N) { return ((N + 3) / 4) * 4 + GPAD; }
 
 struct Variant {
   int nb;    // panel width
@@ -66,8 +70,16 @@ SlotLayout slot_layout(int max_m, int max_n, int nb) {
   return L;
 }
 
-size_t smem_floats(int nb) {
-  return GBK * (16 + 256 + 2 * GPAD)       // product staging (largest: 16 x 256 tiles)
+// Product staging: three ring slots of the largest tile shape (16 x 256), or W and
+// a 256-row chunk of V for the rank-nb updates, whichever is larger.
+__host__ __device__ inline size_t stage_floats(int nb, int max_n) {
+  const size_t gemm = 3 * (size_t)GBK * (16 + 256 + 2 * GPAD);
+  const size_t rank = (size_t)nb * rank_ws_ld(max_n) + (size_t)nb * (RC + GPAD);
+  return gemm > rank ? gemm : rank;
+}
+
+size_t smem_floats(int nb, int max_n) {
+  return stage_floats(nb, max_n)           // product staging
          + 2 * (size_t)nb * (nb + 1)       // Gram, T
          + (size_t)nb * nb / 2             // T recursion scratch
          + (size_t)(BT / 32) * nb          // per-warp sums
@@ -89,23 +101,32 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+__device__ __forceinline__ void cp_async4(float *dst_smem, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // C (M x N, ldc) = alpha op(A) B + beta C; op(A)(i,k) = A[i + k lda] (TA false)
 // or A[k + i lda] (TA true); B(k,j) = B[k + j ldb].  beta == 0: C is not read.
 // Tiles of BM x (4096 / BM), 4 x 4 outputs per thread, K in steps of 16
-// staged through shared memory with the next step prefetched into
-// registers.  BM = 16 or 32 fits the skinny products of the compact-WY
-// updates (M = panel width).  Ends with a barrier, so C is visible to the
-// whole CTA on return.
+// through a 3-stage shared-memory ring filled by cp.async: two steps are in
+// flight while one is multiplied, one barrier per step.  BM = 16 or 32 fits
+// the skinny products of the compact-WY updates (M = panel width).  Ends with
+// a barrier, so C is visible to the whole CTA on return.
 template <bool TA, int BM>
 __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const float *A, int lda, const float *B,
                                       int ldb, float beta, float *C, int ldc, float *stage) {
   constexpr int BN = 4096 / BM;
   constexpr int LA = BM * GBK / BT, LB = BN * GBK / BT;
   constexpr int TXN = BM / 4;
-  float(*As)[BM + GPAD] = reinterpret_cast<float(*)[BM + GPAD]>(stage);
-  float(*Bs)[BN + GPAD] = reinterpret_cast<float(*)[BN + GPAD]>(stage + GBK * (BM + GPAD));
+  constexpr int BUF = GBK * (BM + BN + 2 * GPAD);
+  constexpr int NSTAGE = 3;
   const int tid = threadIdx.x, tx = tid % TXN, ty = tid / TXN;
   const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  const int nk = (K + GBK - 1) / GBK;
   for (int t = 0; t < tm * tn; ++t) {
     const int m0 = (t % tm) * BM, n0 = (t / tm) * BN;
     float acc[4][4];
@@ -113,41 +134,41 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
     for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
-    float ra[LA], rb[LB];
-    auto load = [&](int k0) {
+    auto issue = [&](int step) {  // step < nk: async copies of K-step `step` into its ring slot
+      const int k0 = step * GBK, buf = step % NSTAGE;
+      float(*As)[BM + GPAD] = reinterpret_cast<float(*)[BM + GPAD]>(stage + buf * BUF);
+      float(*Bs)[BN + GPAD] = reinterpret_cast<float(*)[BN + GPAD]>(stage + buf * BUF + GBK * (BM + GPAD));
 #pragma unroll
       for (int s = 0; s < LA; ++s) {
         const int e = tid + s * BT;
         int i, kk;
         if (TA) { kk = e % GBK; i = e / GBK; } else { i = e % BM; kk = e / BM; }
         const int gi = m0 + i, gk = k0 + kk;
-        ra[s] = (gi < M && gk < K) ? (TA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda]) : 0.f;
+        if (gi < M && gk < K) cp_async4(&As[kk][i], TA ? A + gk + (long long)gi * lda : A + gi + (long long)gk * lda);
+        else As[kk][i] = 0.f;
       }
 #pragma unroll
       for (int s = 0; s < LB; ++s) {
         const int e = tid + s * BT;
         const int kb = e % GBK, j = e / GBK;
         const int gk = k0 + kb, gj = n0 + j;
-        rb[s] = (gk < K && gj < N) ? B[gk + (long long)gj * ldb] : 0.f;
+        if (gk < K && gj < N) cp_async4(&Bs[kb][j], B + gk + (long long)gj * ldb);
+        else Bs[kb][j] = 0.f;
       }
     };
-    if (K > 0) load(0);
-    for (int k0 = 0; k0 < K; k0 += GBK) {
-      __syncthreads();  // the previous step is done with the staging buffers
-#pragma unroll
-      for (int s = 0; s < LA; ++s) {
-        const int e = tid + s * BT;
-        int i, kk;
-        if (TA) { kk = e % GBK; i = e / GBK; } else { i = e % BM; kk = e / BM; }
-        As[kk][i] = ra[s];
-      }
-#pragma unroll
-      for (int s = 0; s < LB; ++s) {
-        const int e = tid + s * BT;
-        Bs[e % GBK][e / GBK] = rb[s];
-      }
-      __syncthreads();
-      if (k0 + GBK < K) load(k0 + GBK);
+    // prologue: steps 0 and 1 in flight (a group is committed even when empty)
+    if (nk > 0) issue(0);
+    cp_async_commit();
+    if (nk > 1) issue(1);
+    cp_async_commit();
+    for (int step = 0; step < nk; ++step) {
+      cp_async_wait<1>();  // this thread's copies of `step` have landed
+      __syncthreads();     // ... and everyone's; slot (step + 2) % 3 was last read at step - 1
+      if (step + 2 < nk) issue(step + 2);
+      cp_async_commit();
+      const int buf = step % NSTAGE;
+      const float(*As)[BM + GPAD] = reinterpret_cast<const float(*)[BM + GPAD]>(stage + buf * BUF);
+      const float(*Bs)[BN + GPAD] = reinterpret_cast<const float(*)[BN + GPAD]>(stage + buf * BUF + GBK * (BM + GPAD));
 #pragma unroll
       for (int kk = 0; kk < GBK; ++kk) {
         const float4 a = *reinterpret_cast<const float4 *>(&As[kk][4 * tx]);
@@ -159,6 +180,8 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
           for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
       }
     }
+    cp_async_wait<0>();
+    __syncthreads();  // every slot is free before the next tile's prologue
     // epilogue: all old values of C are read before any is written
     float old[4][4];
 #pragma unroll
@@ -177,6 +200,83 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
       for (int r = 0; r < 4; ++r) {
         const int gi = m0 + 4 * tx + r;
         if (gi < M && gj < N) C[gi + (long long)gj * ldc] = fmaf(alpha, acc[r][c], beta * old[r][c]);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// C(0:M, 0:N) += alpha V(0:M, 0:K) W(0:K, 0:N) for K <= NB (the rank-NB
+// updates of the compact-WY blocks).  W and a chunk of RC rows of V are staged
+// in shared memory once; every 64 x 64 tile of the chunk is then computed from
+// shared memory without further barriers.
+template <int NB>
+__device__ __noinline__ void cta_rank_update(int M, int N, int K, float alpha, const float *V, int ldv,
+                                             const float *W, int ldw, float *C, int ldc, float *stage) {
+  const int wld = rank_ws_ld(N);
+  float *Ws = stage;                   // NB x wld, row k = W(k, :)
+  float *Vs = stage + NB * wld;        // NB x (RC + GPAD), row k = V(chunk rows, k)
+  constexpr int VLD = RC + GPAD;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int e = tid; e < NB * N; e += BT) {
+    const int k = e % NB, c = e / NB;
+    Ws[k * wld + c] = (k < K) ? W[k + (long long)c * ldw] : 0.f;
+  }
+  for (int r0 = 0; r0 < M; r0 += RC) {
+    const int rows = min(RC, M - r0);
+    __syncthreads();  // W staged / the previous chunk is done with Vs
+    for (int e = tid; e < NB * RC; e += BT) {
+      const int r = e % RC, k = e / RC;
+      Vs[k * VLD + r] = (k < K && r < rows) ? V[(r0 + r) + (long long)k * ldv] : 0.f;
+    }
+    __syncthreads();
+    const int tm = (rows + 63) / 64, tn = (N + 63) / 64;
+    // the old C of tile t + 1 is loaded while tile t is multiplied
+    float nxt[4][4];
+    auto load_c = [&](int t) {
+      const int m0 = (t % tm) * 64, n0 = (t / tm) * 64;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int gj = n0 + 4 * ty + c;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int gi = m0 + 4 * tx + r;
+          nxt[r][c] = (gi < rows && gj < N) ? C[(r0 + gi) + (long long)gj * ldc] : 0.f;
+        }
+      }
+    };
+    if (tm * tn > 0) load_c(0);
+    for (int t = 0; t < tm * tn; ++t) {
+      const int m0 = (t % tm) * 64, n0 = (t / tm) * 64;
+      float old[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) old[r][c] = nxt[r][c];
+      if (t + 1 < tm * tn) load_c(t + 1);
+      float acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        const float4 a = *reinterpret_cast<const float4 *>(&Vs[k * VLD + m0 + 4 * tx]);
+        const float4 b = *reinterpret_cast<const float4 *>(&Ws[k * wld + n0 + 4 * ty]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int gj = n0 + 4 * ty + c;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int gi = m0 + 4 * tx + r;
+          if (gi < rows && gj < N) C[(r0 + gi) + (long long)gj * ldc] = fmaf(alpha, acc[r][c], old[r][c]);
+        }
       }
     }
   }
@@ -391,7 +491,7 @@ __device__ __noinline__ void cta_qr_factor(int rows_all, int cols, float *F, int
       float *Cp = F + j0 + (long long)(j0 + bw) * ldf;
       cta_gemm<true, NB>(bw, nc, rows, 1.f, Vp, ldvs, Cp, ldf, 0.f, Wg, NB, sm.stage);
       cta_gemm<true, NB>(bw, nc, bw, 1.f, Tp, NB, Wg, NB, 0.f, Wg2, NB, sm.stage);
-      cta_gemm<false, 64>(rows, nc, bw, -1.f, Vp, ldvs, Wg2, NB, 1.f, Cp, ldf, sm.stage);
+      cta_rank_update<NB>(rows, nc, bw, -1.f, Vp, ldvs, Wg2, NB, Cp, ldf, sm.stage);
     }
   }
 }
@@ -417,7 +517,7 @@ __device__ __noinline__ void cta_qr_form(int rows_all, int cols, const float *F,
     float *Qp = Q + j0 + (long long)j0 * ldq;
     cta_gemm<true, NB>(bw, nc, rows, 1.f, Vp, ldvs, Qp, ldq, 0.f, Wg, NB, sm.stage);
     cta_gemm<false, NB>(bw, nc, bw, 1.f, Tp, NB, Wg, NB, 0.f, Wg2, NB, sm.stage);
-    cta_gemm<false, 64>(rows, nc, bw, -1.f, Vp, ldvs, Wg2, NB, 1.f, Qp, ldq, sm.stage);
+    cta_rank_update<NB>(rows, nc, bw, -1.f, Vp, ldvs, Wg2, NB, Qp, ldq, sm.stage);
   }
   for (long long e = tid; e < (long long)rows_all * cols; e += BT) {
     const int i = (int)(e % rows_all), j = (int)(e / rows_all);
@@ -490,7 +590,7 @@ __global__ void __launch_bounds__(BT, MINB) urv_batched_kernel(Params p) {
   float *sf = reinterpret_cast<float *>(smem_raw);
   Smem sm;
   sm.stage = sf;
-  sm.Gm = sm.stage + GBK * (16 + 256 + 2 * GPAD);
+  sm.Gm = sm.stage + stage_floats(NB, p.max_n);
   sm.Tt = sm.Gm + NB * (NB + 1);
   sm.tmp = sm.Tt + NB * (NB + 1);
   sm.part = sm.tmp + NB * NB / 2;
@@ -579,25 +679,34 @@ KernelFn variant_kernel(int v) {
   }
 }
 
-// CTAs per SM that variant v reaches for max_m (0 if it cannot run).  The
-// first query per (device, variant, max_m) also raises the kernel's dynamic
-// shared-memory limit; later ones (e.g. during stream capture) only read the
-// cache.
+// CTAs per SM that variant v reaches for (max_m, max_n) (0 if it cannot run).
+// The kernel's dynamic shared-memory limit is a property of the function, not
+// of the query: it is only ever raised (to the largest size any query needed),
+// so a later query for smaller matrices cannot invalidate the launch of a
+// larger batch whose occupancy was cached earlier.  Results are cached per
+// (device, variant, max_m, max_n), so queries made during stream capture only
+// read the cache.
 std::mutex g_occ_mu;
-std::map<std::tuple<int, int, int>, int> g_occ;
+std::map<std::tuple<int, int, int, int>, int> g_occ;
+std::map<std::pair<int, int>, size_t> g_smem_attr;  // (device, variant) -> limit set
 
-int variant_occupancy(int v, int max_m) {
+int variant_occupancy(int v, int max_m, int max_n) {
   const DeviceInfo *di = device_info();
   if (!di) return 0;
   std::lock_guard<std::mutex> lock(g_occ_mu);
-  const auto key = std::make_tuple(di->device, v, max_m);
+  const auto key = std::make_tuple(di->device, v, max_m, max_n);
   auto it = g_occ.find(key);
   if (it != g_occ.end()) return it->second;
   int occ = 0;
-  const size_t smem = smem_floats(kVariants[v].nb) * sizeof(float);
+  const size_t smem = smem_floats(kVariants[v].nb, max_n) * sizeof(float);
   KernelFn fn = variant_kernel(v);
-  if (max_m <= kVariants[v].rpt * BT && smem <= (size_t)di->max_smem_optin &&
-      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess) {
+  size_t &limit = g_smem_attr[std::make_pair(di->device, v)];
+  bool ok = max_m <= kVariants[v].rpt * BT && smem <= (size_t)di->max_smem_optin;
+  if (ok && smem > limit) {
+    ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+    if (ok) limit = smem;
+  }
+  if (ok) {
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, BT, smem) == cudaSuccess)
       occ = blocks < kVariants[v].minb ? blocks : kVariants[v].minb;
@@ -610,16 +719,16 @@ int variant_occupancy(int v, int max_m) {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int>, int> g_tuned;  // (device, count, max_m, max_n, q, reorth)
 
-int default_variant(int max_m) {
+int default_variant(int max_m, int max_n) {
   for (int v = 0; v < kNumVariants; ++v)
-    if (variant_occupancy(v, max_m) > 0) return v;
+    if (variant_occupancy(v, max_m, max_n) > 0) return v;
   return -1;
 }
 
 size_t workspace_for(int max_m, int max_n, int v, int *slots_out) {
   const DeviceInfo *di = device_info();
   if (!di) return 0;
-  const int occ = variant_occupancy(v, max_m);
+  const int occ = variant_occupancy(v, max_m, max_n);
   if (occ <= 0) return 0;
   const int slots = di->num_sms * occ;
   if (slots_out) *slots_out = slots;
@@ -658,7 +767,7 @@ int launch_batched(int count, const purl_batch_item *items, int max_m, int max_n
     batched_reset_kernel<<<1, 1, 0, s>>>(p.hdr); }
   PURL_CUDA_TRY(cudaGetLastError());
   if (grid == 0) return PURL_OK;
-  const size_t smem = smem_floats(kVariants[v].nb) * sizeof(float);
+  const size_t smem = smem_floats(kVariants[v].nb, max_n) * sizeof(float);
   { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "urv_batched_kernel");
     variant_kernel(v)<<<grid, BT, smem, s>>>(p); }
   PURL_CUDA_TRY(cudaGetLastError());
@@ -713,7 +822,7 @@ int purl_urv_factor_batched(int count, const purl_batch_item *items, int max_m, 
   if (v < 0) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tuned.find(std::make_tuple(device_info()->device, count, max_m, max_n, q, reorth ? 1 : 0));
-    v = it != g_tuned.end() ? it->second : default_variant(max_m);
+    v = it != g_tuned.end() ? it->second : default_variant(max_m, max_n);
   }
   if (v < 0) return PURL_ERR_UNSUPPORTED;
   return launch_batched(count, items, max_m, max_n, q, reorth, v, workspace, workspace_bytes, stream);
