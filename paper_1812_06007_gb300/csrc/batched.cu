@@ -5,9 +5,10 @@
 // in array order: put the costliest first for load balance) and runs the
 // whole factorization of one matrix by itself: Gaussian G, q power steps
 // with re-orthonormalisation, the QR of Eq. (5), A V and the QR of Eq. (6).
-// Per matrix the data are small (m <= 1024, n <= 512), so the working set of
-// a CTA stays in L2 and nothing waits on another CTA -- no grid barrier, no
-// spin-wait.  Building blocks, all CTA-wide:
+// Per matrix the data are small (m <= 1024, n <= 512): a CTA's scratch slot
+// holds one m x n and one n x n iterate and the T factors (Householder
+// vectors stay in place below the factored matrix's diagonal), and nothing
+// waits on another CTA -- no grid barrier, no spin-wait.  Building blocks, all CTA-wide:
 //   cta_gemm      C = alpha op(A) B + beta C, 64x64 register tiles of FP32 FFMA
 //                 staged through shared memory (4x4 outputs per thread)
 //   panel_factor  unblocked Householder on an NB-column panel held in shared
@@ -52,7 +53,7 @@ struct BatchHeader {
 };
 
 struct SlotLayout {
-  size_t Sm, Sn, Vs, Wg, Wg2, Ts, total;  // offsets in floats
+  size_t Sm, Sn, Wg, Wg2, Ts, total;  // offsets in floats
 };
 
 __host__ __device__ size_t round64(size_t x) { return (x + 63) / 64 * 64; }
@@ -62,7 +63,6 @@ SlotLayout slot_layout(int max_m, int max_n, int nb) {
   size_t o = 0;
   L.Sm = o;  o += round64((size_t)max_m * max_n);
   L.Sn = o;  o += round64((size_t)max_n * max_n);
-  L.Vs = o;  o += round64((size_t)max_m * max_n);
   L.Wg = o;  o += round64((size_t)nb * max_n);
   L.Wg2 = o; o += round64((size_t)nb * max_n);
   L.Ts = o;  o += round64((size_t)((max_n + nb - 1) / nb) * nb * nb);
@@ -114,9 +114,11 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Tiles of BM x (4096 / BM), 4 x 4 outputs per thread, K in steps of 16
 // through a 3-stage shared-memory ring filled by cp.async: two steps are in
 // flight while one is multiplied, one barrier per step.  BM = 16 or 32 fits
-// the skinny products of the compact-WY updates (M = panel width).  Ends with
-// a barrier, so C is visible to the whole CTA on return.
-template <bool TA, int BM>
+// the skinny products of the compact-WY updates (M = panel width).  With
+// UNITV (TA only), A holds Householder vectors in place below a diagonal:
+// op(A)(i, k) = A(k, i) for k > i, 1 for k == i, 0 for k < i.  Ends with a
+// barrier, so C is visible to the whole CTA on return.
+template <bool TA, int BM, bool UNITV = false>
 __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const float *A, int lda, const float *B,
                                       int ldb, float beta, float *C, int ldc, float *stage) {
   constexpr int BN = 4096 / BM;
@@ -144,8 +146,10 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
         int i, kk;
         if (TA) { kk = e % GBK; i = e / GBK; } else { i = e % BM; kk = e / BM; }
         const int gi = m0 + i, gk = k0 + kk;
-        if (gi < M && gk < K) cp_async4(&As[kk][i], TA ? A + gk + (long long)gi * lda : A + gi + (long long)gk * lda);
-        else As[kk][i] = 0.f;
+        if (gi < M && gk < K && !(UNITV && gk <= gi))
+          cp_async4(&As[kk][i], TA ? A + gk + (long long)gi * lda : A + gi + (long long)gk * lda);
+        else
+          As[kk][i] = (UNITV && gi < M && gk == gi) ? 1.f : 0.f;
       }
 #pragma unroll
       for (int s = 0; s < LB; ++s) {
@@ -207,10 +211,11 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
 }
 
 // C(0:M, 0:N) += alpha V(0:M, 0:K) W(0:K, 0:N) for K <= NB (the rank-NB
-// updates of the compact-WY blocks).  W and a chunk of RC rows of V are staged
+// updates of the compact-WY blocks; with UNITV, V is read as Householder
+// vectors stored in place: 1 on its diagonal, 0 above).  W and a chunk of RC rows of V are staged
 // in shared memory once; every 64 x 64 tile of the chunk is then computed from
 // shared memory without further barriers.
-template <int NB>
+template <int NB, bool UNITV = false>
 __device__ __noinline__ void cta_rank_update(int M, int N, int K, float alpha, const float *V, int ldv,
                                              const float *W, int ldw, float *C, int ldc, float *stage) {
   const int wld = rank_ws_ld(N);
@@ -227,7 +232,10 @@ __device__ __noinline__ void cta_rank_update(int M, int N, int K, float alpha, c
     __syncthreads();  // W staged / the previous chunk is done with Vs
     for (int e = tid; e < NB * RC; e += BT) {
       const int r = e % RC, k = e / RC;
-      Vs[k * VLD + r] = (k < K && r < rows) ? V[(r0 + r) + (long long)k * ldv] : 0.f;
+      const int gr = r0 + r;  // with UNITV, V(gr, k) is 1 on the diagonal and 0 above it
+      Vs[k * VLD + r] = (k < K && r < rows)
+                            ? ((!UNITV || gr > k) ? V[gr + (long long)k * ldv] : (gr == k ? 1.f : 0.f))
+                            : 0.f;
     }
     __syncthreads();
     const int tm = (rows + 63) / 64, tn = (N + 63) / 64;
@@ -372,9 +380,10 @@ __device__ void build_T(int bw, const Smem &sm, float *Tp) {
 }
 
 // Householder QR of the rows x cols matrix F (in place; ldf), compact WY with
-// panels of NB columns.  Writes the explicit V of every panel to Vs (ldvs),
-// its T (column-major, NB x NB) to Ts + panel * NB * NB, and leaves R on and
-// above F's diagonal (beta_j on the diagonal, before any sign change).
+// panels of NB columns.  Leaves R on and above F's diagonal (beta_j on the
+// diagonal, before any sign change) and the Householder vectors below it
+// (their unit leading entries implicit), and writes every panel's T
+// (column-major, NB x NB) to Ts + panel * NB * NB.
 //
 // The panel lives in registers: thread t holds rows t, t + 256, ... (RPT of
 // them) of all NB columns.  Column k takes one CTA-wide reduction of
@@ -383,7 +392,7 @@ __device__ void build_T(int bw, const Smem &sm, float *Tp) {
 // columns c > k, and the Gram entries g[l][k] = v_l . v_k (l < k) that the
 // T factor needs; then every thread updates its own rows.
 template <int NB, int RPT>
-__device__ __noinline__ void cta_qr_factor(int rows_all, int cols, float *F, int ldf, float *Vs, int ldvs, float *Ts,
+__device__ __noinline__ void cta_qr_factor(int rows_all, int cols, float *F, int ldf, float *Ts,
                                            float *Wg, float *Wg2, const Smem &sm) {
   constexpr int PS = NB + 1;
   constexpr int NW = BT / 32;
@@ -467,7 +476,7 @@ __device__ __noinline__ void cta_qr_factor(int rows_all, int cols, float *F, int
       }
       if (tid == k) x[0][k] = sm.beta[k];
     }
-    // ---- write back: explicit V, and R on and above the diagonal ----
+    // ---- write back: R on and above the diagonal, V below it ----
 #pragma unroll
     for (int s = 0; s < RPT; ++s) {
       const int r = tid + s * BT;
@@ -475,8 +484,7 @@ __device__ __noinline__ void cta_qr_factor(int rows_all, int cols, float *F, int
 #pragma unroll
         for (int c = 0; c < NB; ++c) {
           if (c < bw) {
-            Vs[(j0 + r) + (long long)(j0 + c) * ldvs] = r > c ? x[s][c] : (r == c ? 1.f : 0.f);
-            if (r <= c) F[(j0 + r) + (long long)(j0 + c) * ldf] = x[s][c];
+            F[(j0 + r) + (long long)(j0 + c) * ldf] = x[s][c];
           }
         }
       }
@@ -487,20 +495,20 @@ __device__ __noinline__ void cta_qr_factor(int rows_all, int cols, float *F, int
     // ---- trailing update C -= V T^T (V^T C) ----
     const int nc = cols - j0 - bw;
     if (nc > 0) {
-      const float *Vp = Vs + j0 + (long long)j0 * ldvs;
+      const float *Vp = F + j0 + (long long)j0 * ldf;
       float *Cp = F + j0 + (long long)(j0 + bw) * ldf;
-      cta_gemm<true, NB>(bw, nc, rows, 1.f, Vp, ldvs, Cp, ldf, 0.f, Wg, NB, sm.stage);
+      cta_gemm<true, NB, true>(bw, nc, rows, 1.f, Vp, ldf, Cp, ldf, 0.f, Wg, NB, sm.stage);
       cta_gemm<true, NB>(bw, nc, bw, 1.f, Tp, NB, Wg, NB, 0.f, Wg2, NB, sm.stage);
-      cta_rank_update<NB>(rows, nc, bw, -1.f, Vp, ldvs, Wg2, NB, Cp, ldf, sm.stage);
+      cta_rank_update<NB, true>(rows, nc, bw, -1.f, Vp, ldf, Wg2, NB, Cp, ldf, sm.stage);
     }
   }
 }
 
 // Q (rows x cols, ldq) = H_1 ... H_cols [I; 0] from the panels cta_qr_factor
-// left in Vs and Ts, then the sign fix diag(R) >= 0 read from F's diagonal;
+// left in F (below its diagonal) and Ts, then the sign fix diag(R) >= 0 read from F's diagonal;
 // R (cols x cols, ldr) is written when non-null.
 template <int NB>
-__device__ __noinline__ void cta_qr_form(int rows_all, int cols, const float *F, int ldf, const float *Vs, int ldvs,
+__device__ __noinline__ void cta_qr_form(int rows_all, int cols, const float *F, int ldf,
                             const float *Ts, float *Wg, float *Wg2, float *Q, int ldq, float *R, int ldr,
                             const Smem &sm) {
   const int tid = threadIdx.x;
@@ -512,12 +520,12 @@ __device__ __noinline__ void cta_qr_form(int rows_all, int cols, const float *F,
   const int npan = (cols + NB - 1) / NB;
   for (int p = npan - 1; p >= 0; --p) {
     const int j0 = p * NB, bw = min(NB, cols - j0), rows = rows_all - j0, nc = cols - j0;
-    const float *Vp = Vs + j0 + (long long)j0 * ldvs;
+    const float *Vp = F + j0 + (long long)j0 * ldf;
     const float *Tp = Ts + (size_t)p * NB * NB;
     float *Qp = Q + j0 + (long long)j0 * ldq;
-    cta_gemm<true, NB>(bw, nc, rows, 1.f, Vp, ldvs, Qp, ldq, 0.f, Wg, NB, sm.stage);
+    cta_gemm<true, NB, true>(bw, nc, rows, 1.f, Vp, ldf, Qp, ldq, 0.f, Wg, NB, sm.stage);
     cta_gemm<false, NB>(bw, nc, bw, 1.f, Tp, NB, Wg, NB, 0.f, Wg2, NB, sm.stage);
-    cta_rank_update<NB>(rows, nc, bw, -1.f, Vp, ldvs, Wg2, NB, Qp, ldq, sm.stage);
+    cta_rank_update<NB, true>(rows, nc, bw, -1.f, Vp, ldf, Wg2, NB, Qp, ldq, sm.stage);
   }
   for (long long e = tid; e < (long long)rows_all * cols; e += BT) {
     const int i = (int)(e % rows_all), j = (int)(e / rows_all);
@@ -601,7 +609,7 @@ __global__ void __launch_bounds__(BT, MINB) urv_batched_kernel(Params p) {
   sm.scale = sm.beta + NB;
   sm.scal = reinterpret_cast<int *>(sm.scale + NB);
   float *slot = p.scratch + (size_t)blockIdx.x * p.slot_floats;
-  float *Sm = slot + p.L.Sm, *Sn = slot + p.L.Sn, *Vs = slot + p.L.Vs;
+  float *Sm = slot + p.L.Sm, *Sn = slot + p.L.Sn;
   float *Wg = slot + p.L.Wg, *Wg2 = slot + p.L.Wg2, *Ts = slot + p.L.Ts;
   while (true) {
     if (threadIdx.x == 0) sm.scal[0] = (int)atomicAdd(&p.hdr->next, 1u);
@@ -625,8 +633,8 @@ __global__ void __launch_bounds__(BT, MINB) urv_batched_kernel(Params p) {
       const float *Z = Sm;
       int ldz = m;
       if (p.reorth) {
-        cta_qr_factor<NB, RPT>(m, n, Sm, m, Vs, m, Ts, Wg, Wg2, sm);
-        cta_qr_form<NB>(m, n, Sm, m, Vs, m, Ts, Wg, Wg2, it.U, it.ldu, nullptr, 0, sm);
+        cta_qr_factor<NB, RPT>(m, n, Sm, m, Ts, Wg, Wg2, sm);
+        cta_qr_form<NB>(m, n, Sm, m, Ts, Wg, Wg2, it.U, it.ldu, nullptr, 0, sm);
         Z = it.U;
         ldz = it.ldu;
       }
@@ -634,20 +642,20 @@ __global__ void __launch_bounds__(BT, MINB) urv_batched_kernel(Params p) {
       Y = Sn;
       ldy = n;
       if (p.reorth && i < p.q) {
-        cta_qr_factor<NB, RPT>(n, n, Sn, n, Vs, n, Ts, Wg, Wg2, sm);
-        cta_qr_form<NB>(n, n, Sn, n, Vs, n, Ts, Wg, Wg2, it.V, it.ldv, nullptr, 0, sm);
+        cta_qr_factor<NB, RPT>(n, n, Sn, n, Ts, Wg, Wg2, sm);
+        cta_qr_form<NB>(n, n, Sn, n, Ts, Wg, Wg2, it.V, it.ldv, nullptr, 0, sm);
         Y = it.V;
         ldy = it.ldv;
       }
     }
     if (Y != Sn) cta_copy(n, n, Y, ldy, Sn, n);
     // Eq. (5): Y_q = V Z'
-    cta_qr_factor<NB, RPT>(n, n, Sn, n, Vs, n, Ts, Wg, Wg2, sm);
-    cta_qr_form<NB>(n, n, Sn, n, Vs, n, Ts, Wg, Wg2, it.V, it.ldv, nullptr, 0, sm);
+    cta_qr_factor<NB, RPT>(n, n, Sn, n, Ts, Wg, Wg2, sm);
+    cta_qr_form<NB>(n, n, Sn, n, Ts, Wg, Wg2, it.V, it.ldv, nullptr, 0, sm);
     // Eq. (6): A V = U R
     cta_gemm<false, 64>(m, n, n, 1.f, it.A, it.lda, it.V, it.ldv, 0.f, Sm, m, sm.stage);
-    cta_qr_factor<NB, RPT>(m, n, Sm, m, Vs, m, Ts, Wg, Wg2, sm);
-    cta_qr_form<NB>(m, n, Sm, m, Vs, m, Ts, Wg, Wg2, it.U, it.ldu, it.R, it.ldr, sm);
+    cta_qr_factor<NB, RPT>(m, n, Sm, m, Ts, Wg, Wg2, sm);
+    cta_qr_form<NB>(m, n, Sm, m, Ts, Wg, Wg2, it.U, it.ldu, it.R, it.ldr, sm);
   }
 }
 
