@@ -373,6 +373,10 @@ def probe_errors(A, U, R, V, k: int = 16):
 
 
 def end_to_end(a, A, U, R, V, ws, mode, seed, world, dev, B):
+    """Same factorization through the public API with host memory on both ends: every step copies A
+    from pinned host memory to the device and U, R, V back.  Copies run on their own stream and
+    device buffers are doubled, so step i's copies overlap the neighbouring steps' factorizations;
+    the timed region runs from the first H2D copy to the last D2H copy."""
     import torch
     m, n = A.shape
     hA = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
@@ -380,29 +384,49 @@ def end_to_end(a, A, U, R, V, ws, mode, seed, world, dev, B):
     hU = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
     hR = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
     hV = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
-    dA = B.empty_colmajor(m, n, dev)
-    stream = torch.cuda.current_stream()
+    dA = [B.empty_colmajor(m, n, dev) for _ in range(2)]
+    outs = [(U, R, V), (B.empty_colmajor(m, n, dev), B.empty_colmajor(n, n, dev), B.empty_colmajor(n, n, dev))]
+    comp = torch.cuda.current_stream()
+    copy = torch.cuda.Stream(device=dev)
+    ev = lambda: torch.cuda.Event()
+    a_ready, a_free = [ev(), ev()], [ev(), ev()]
+    done, out_free = [ev(), ev()], [ev(), ev()]
+    for e in a_free + out_free:
+        e.record(comp)
 
-    def step():
-        dA.copy_(hA, non_blocking=True)
-        B.purl_urv_factor(dA, a.q, a.reorth, seed, mode=mode, out=(U, R, V), workspace=ws, stream=stream)
-        hU.copy_(U, non_blocking=True)
-        hR.copy_(R, non_blocking=True)
-        hV.copy_(V, non_blocking=True)
+    def step(i):
+        b = i % 2
+        with torch.cuda.stream(copy):
+            copy.wait_event(a_free[b])
+            dA[b].copy_(hA, non_blocking=True)
+            a_ready[b].record(copy)
+        comp.wait_event(a_ready[b])
+        comp.wait_event(out_free[b])
+        Ub, Rb, Vb = outs[b]
+        B.purl_urv_factor(dA[b], a.q, a.reorth, seed, mode=mode, out=(Ub, Rb, Vb), workspace=ws, stream=comp)
+        done[b].record(comp)
+        a_free[b].record(comp)
+        with torch.cuda.stream(copy):
+            copy.wait_event(done[b])
+            hU.copy_(Ub, non_blocking=True)
+            hR.copy_(Rb, non_blocking=True)
+            hV.copy_(Vb, non_blocking=True)
+            out_free[b].record(copy)
 
-    step()
+    step(0)
     torch.cuda.synchronize()
     steps = max(1, min(a.steps, 3))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        step()
-    e1.record(stream)
+    e0.record(copy)
+    comp.wait_event(e0)
+    for i in range(steps):
+        step(i)
+    e1.record(copy)
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
     return {"value": urv_flops(m, n, a.q, a.reorth) * world / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
             "ms_per_step": ms, "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * (m * n + 2 * n * n),
-            "steps": steps}
+            "steps": steps, "pipelined": "copies on their own stream, double-buffered device inputs and outputs"}
 
 
 def _peaks():
