@@ -21,6 +21,9 @@
 // to the first n columns of the identity; the signs are then normalised so
 // that diag(R) >= 0 (the convention of the footnote in Section 2.2 that makes
 // the factorization unique).
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 #include "qr.cuh"
 #include "profile.cuh"
@@ -361,25 +364,32 @@ int grid_for(long long total, const DeviceInfo *di) {
   return (int)(g < 1 ? 1 : g);
 }
 
-// Max co-resident blocks for a panel launch with `smem` dynamic bytes.
+// Max co-resident blocks for a panel launch with `smem` dynamic bytes.  The
+// panel's shared memory changes with every panel (rows shrink), so results
+// are cached per 4 KB step of shared memory, computed for the step's upper
+// end (capacity only falls as shared memory grows); the kernel's dynamic
+// shared-memory limit is only ever raised.
 int panel_capacity(const DeviceInfo *di, size_t smem) {
-  static thread_local int cached_dev = -1;
-  static thread_local size_t cached_smem = 0;
-  static thread_local int cached_cap = 0;
-  if (cached_dev == di->device && cached_smem == smem) return cached_cap;
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, int> cache;
+  static std::map<int, size_t> limit;
+  const size_t step = (smem + 4095) / 4096 * 4096;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(di->device, step);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  const size_t want = step < (size_t)di->max_smem_optin ? step : (size_t)di->max_smem_optin;
+  size_t &lim = limit[di->device];
+  if (want > 48 * 1024 && want > lim) {
+    if (cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want) != cudaSuccess)
       return 0;
+    lim = want;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, PNT, smem) !=
-      cudaSuccess)
-    return 0;
-  cached_dev = di->device;
-  cached_smem = smem;
-  cached_cap = per_sm * di->num_sms;
-  return cached_cap;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, PNT, want) != cudaSuccess) return 0;
+  const int cap = per_sm * di->num_sms;
+  cache[key] = cap;
+  return cap;
 }
 
 }  // namespace
