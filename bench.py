@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip per-kernel event timing")
     ap.add_argument("--workload", choices=["urv", "batched", "adjoint", "rsvd"], default="urv")
+    ap.add_argument("--matrix", choices=["haar", "gaussian"], default="haar",
+                    help="urv: Haar-factor matrix with sigma_j = 10^(-6(j-1)/(n-1)), or Gaussian entries")
     ap.add_argument("--rank", type=int, default=256, help="rsvd: target rank l")
     ap.add_argument("--count", type=int, default=4096, help="batched: number of matrices")
     ap.add_argument("--variant", type=int, default=-1, help="batched: kernel variant (-1 = autotune)")
@@ -227,8 +229,10 @@ def run_ours(a):
     mode = B.PURL_MODE_MIXED_BF16 if a.mode == "mixed" else B.PURL_MODE_FP64
     m, n, q, reorth = a.m, a.n, a.q, a.reorth
 
-    sigma = W.sigma_profile("exponential", n, decades=6)
-    A = W.test_matrix_torch(m, n, sigma, device=dev)
+    if a.matrix == "gaussian":
+        A = W.gaussian_matrix_torch(m, n, 2024 + rank, device=dev)
+    else:
+        A = W.test_matrix_torch(m, n, W.sigma_profile("exponential", n, decades=6), device=dev)
     U = B.empty_colmajor(m, n, dev)
     R = B.empty_colmajor(n, n, dev)
     V = B.empty_colmajor(n, n, dev)
@@ -308,7 +312,8 @@ def run_ours(a):
         "vs_baseline": None, "dtype": "bf16+f64" if a.mode == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": f"PowerURV m={m} n={n} q={q} reorth={int(reorth)} {a.mode}",
                    "m": m, "n": n, "q": q, "reorth": reorth, "mode": a.mode,
-                   "sigma": "10^(-6(j-1)/(n-1)), Haar factors", "parallelism": f"replicas{world}",
+                   "matrix": ("Gaussian entries" if a.matrix == "gaussian"
+                              else "Haar factors, sigma 10^(-6(j-1)/(n-1))"), "parallelism": f"replicas{world}",
                    "l2": f"inputs larger than L2 (A is {8 * m * n / 2**30:.1f} GiB)"},
         "sec_per_factorization": ms_step * 1e-3,
         "fp64_path": fp64,
