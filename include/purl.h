@@ -370,6 +370,12 @@ unsigned long long purl_launch_count(void);
  * returns the totals since the last purl_profile_reset (-1 for a bad class). */
 void purl_profile_enable(int on);
 void purl_profile_reset(void);
+/* Sampling stride of the timing (default 1: every launch).  With s > 1 the
+ * first 8 launches of every kernel name and then every s-th are timed, and a
+ * name's (and class's) device time is reported as its timed launches' time
+ * scaled by launches / timed launches; launches, flops and bytes count every
+ * launch made while timing was on. */
+void purl_profile_set_stride(int stride);
 int purl_profile_read(int cls, long long *launches, double *ms, double *flops, double *bytes);
 const char *purl_profile_class_name(int cls);
 /* The same totals per kernel name (index 0, 1, ... until -1 is returned). */

@@ -61,6 +61,7 @@ SIGNATURES = {
     "purl_launch_count": (ctypes.c_ulonglong, []),
     "purl_profile_enable": (None, [_i]),
     "purl_profile_reset": (None, []),
+    "purl_profile_set_stride": (None, [_i]),
     "purl_profile_read": (_i, [_i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_d),
                                ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "purl_profile_class_name": (ctypes.c_char_p, [_i]),
@@ -389,6 +390,10 @@ def purl_launch_count() -> int:
 
 def purl_profile_enable(on: bool = True):
     lib().purl_profile_enable(int(bool(on)))
+
+
+def purl_profile_set_stride(stride: int):
+    lib().purl_profile_set_stride(stride)
 
 
 def purl_profile_reset():
