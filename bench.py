@@ -2,12 +2,15 @@
 """PowerURV throughput on one GB300 (or N replicas), printed as ONE JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--mode mixed|fp64] [--m M] [--n N] [--q Q] [--no-reorth]
-                    [--workload urv|batched|adjoint]
+                    [--mode mixed|fp64|fp64emu] [--m M] [--n N] [--q Q] [--no-reorth]
+                    [--workload urv|batched|adjoint|rsvd]
 
---workload batched times the batched FP32 engine (4096 matrices, n ~ U[16,256],
-m ~ U[n,2n], q = 2, one persistent launch) in matrices/s; --workload adjoint
-times the FP64 reverse mode (m = n = 2048, q = 2) in seconds per backward.
+--mode fp64emu runs the FP64 algorithm with every product emulated on the BF16
+tensor cores (8 fixed-point slices, exact sums).  --workload batched times the
+batched FP32 engine (4096 matrices, n ~ U[16,256], m ~ U[n,2n], q = 2, one
+persistent launch) in matrices/s; --workload adjoint times the FP64 reverse
+mode (m = n = 2048, q = 2) in seconds per backward; --workload rsvd times the
+randomized SVD (m = n = 8192, l = 256).
 The default is the PowerURV factorization below.
 
 A step is one full PowerURV factorization A = U R V^T (Section 3 of the
@@ -64,7 +67,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--mode", choices=["mixed", "fp64", "fp64emu"], default="mixed")
     ap.add_argument("--m", type=int, default=0, help="rows (default n)")
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--q", type=int, default=2)
@@ -226,7 +229,7 @@ def run_ours(a):
     dev = torch.device("cuda", torch.cuda.current_device())
     Bld.build()
     B.lib()
-    mode = B.PURL_MODE_MIXED_BF16 if a.mode == "mixed" else B.PURL_MODE_FP64
+    mode = {"mixed": B.PURL_MODE_MIXED_BF16, "fp64": B.PURL_MODE_FP64, "fp64emu": B.PURL_MODE_FP64_EMU}[a.mode]
     m, n, q, reorth = a.m, a.n, a.q, a.reorth
 
     if a.matrix == "gaussian":
@@ -290,7 +293,7 @@ def run_ours(a):
 
     # ---- the FP64 path on the same recipe (the "vs FP64" of the metric) ----
     fp64 = None
-    if a.mode == "mixed" and a.fp64_n > 0:
+    if a.mode in ("mixed", "fp64emu") and a.fp64_n > 0:
         del ws
         torch.cuda.empty_cache()
         fp64 = fp64_compare(a, dev, B, W, seed)
@@ -313,7 +316,8 @@ def run_ours(a):
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16+f64" if a.mode == "mixed" else "f64", "data": "synthetic",
+        "vs_baseline": None, "data": "synthetic",
+        "dtype": {"mixed": "bf16+f64", "fp64": "f64", "fp64emu": "f64 (emulated: 8 bf16 slices, exact sums)"}[a.mode],
         "config": {"workload": f"PowerURV m={m} n={n} q={q} reorth={int(reorth)} {a.mode}",
                    "m": m, "n": n, "q": q, "reorth": reorth, "mode": a.mode,
                    "matrix": ("Gaussian entries" if a.matrix == "gaussian"
@@ -383,9 +387,10 @@ def probe_errors(A, U, R, V, k: int = 16):
 
 def end_to_end(a, A, U, R, V, ws, mode, seed, world, dev, B):
     """Same factorization through the public API with host memory on both ends: every step copies A
-    from pinned host memory to the device and U, R, V back.  Copies run on their own stream and
-    device buffers are doubled, so step i's copies overlap the neighbouring steps' factorizations;
-    the timed region runs from the first H2D copy to the last D2H copy."""
+    from pinned host memory to the device and U, R, V back.  Host-to-device and device-to-host
+    copies run on two streams of their own and device buffers are doubled, so step i+1's input copy
+    and step i-1's output copies overlap step i's factorization; the timed region runs from the
+    first H2D copy to the last D2H copy.  The copies' own durations are reported beside it."""
     import torch
     m, n = A.shape
     hA = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
@@ -396,46 +401,70 @@ def end_to_end(a, A, U, R, V, ws, mode, seed, world, dev, B):
     dA = [B.empty_colmajor(m, n, dev) for _ in range(2)]
     outs = [(U, R, V), (B.empty_colmajor(m, n, dev), B.empty_colmajor(n, n, dev), B.empty_colmajor(n, n, dev))]
     comp = torch.cuda.current_stream()
-    copy = torch.cuda.Stream(device=dev)
+    h2d, d2h = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
     ev = lambda: torch.cuda.Event()
+    tev = lambda: torch.cuda.Event(enable_timing=True)
     a_ready, a_free = [ev(), ev()], [ev(), ev()]
     done, out_free = [ev(), ev()], [ev(), ev()]
     for e in a_free + out_free:
         e.record(comp)
+    marks = {}
 
-    def step(i):
+    def load(i):
         b = i % 2
-        with torch.cuda.stream(copy):
-            copy.wait_event(a_free[b])
+        mk = marks.setdefault(i, [tev() for _ in range(4)])
+        with torch.cuda.stream(h2d):
+            h2d.wait_event(a_free[b])
+            mk[0].record(h2d)
             dA[b].copy_(hA, non_blocking=True)
-            a_ready[b].record(copy)
+            mk[1].record(h2d)
+            a_ready[b].record(h2d)
+
+    def factor_and_store(i):
+        b = i % 2
+        mk = marks[i]
         comp.wait_event(a_ready[b])
         comp.wait_event(out_free[b])
         Ub, Rb, Vb = outs[b]
         B.purl_urv_factor(dA[b], a.q, a.reorth, seed, mode=mode, out=(Ub, Rb, Vb), workspace=ws, stream=comp)
         done[b].record(comp)
         a_free[b].record(comp)
-        with torch.cuda.stream(copy):
-            copy.wait_event(done[b])
+        with torch.cuda.stream(d2h):
+            d2h.wait_event(done[b])
+            mk[2].record(d2h)
             hU.copy_(Ub, non_blocking=True)
             hR.copy_(Rb, non_blocking=True)
             hV.copy_(Vb, non_blocking=True)
-            out_free[b].record(copy)
+            mk[3].record(d2h)
+            out_free[b].record(d2h)
 
-    step(0)
+    load(0)
+    factor_and_store(0)
     torch.cuda.synchronize()
+    marks.clear()
     steps = max(1, min(a.steps, 3))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(copy)
-    comp.wait_event(e0)
+    e0.record(comp)
+    h2d.wait_event(e0)
+    load(0)
     for i in range(steps):
-        step(i)
-    e1.record(copy)
+        # the next step's input copy is queued before this step's kernels, so it runs beside them
+        if i + 1 < steps:
+            load(i + 1)
+        factor_and_store(i)
+    comp.wait_stream(d2h)
+    e1.record(comp)
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+    h2d_ms = sum(mk[0].elapsed_time(mk[1]) for mk in marks.values()) / steps
+    d2h_ms = sum(mk[2].elapsed_time(mk[3]) for mk in marks.values()) / steps
+    bi, bo = 8 * m * n, 8 * (m * n + 2 * n * n)
     return {"value": urv_flops(m, n, a.q, a.reorth) * world / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
-            "ms_per_step": ms, "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * (m * n + 2 * n * n),
-            "steps": steps, "pipelined": "copies on their own stream, double-buffered device inputs and outputs"}
+            "ms_per_step": ms, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+            "h2d_ms": h2d_ms, "d2h_ms": d2h_ms,
+            "h2d_gbs": bi / (h2d_ms * 1e-3) / 1e9, "d2h_gbs": bo / (d2h_ms * 1e-3) / 1e9,
+            "steps": steps,
+            "pipelined": "H2D and D2H copies on two streams of their own, double-buffered device inputs and outputs"}
 
 
 def _peaks():

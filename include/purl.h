@@ -57,6 +57,13 @@ extern "C" {
  * slices (2 slices in the power iteration's re-orthonormalisations, 4 in the
  * QRs of Eqs. (5)-(6) and in A V); Householder panels in FP64. */
 #define PURL_MODE_MIXED_BF16 2
+/* FP64 emulated on the BF16 tensor cores: the FP64 mode's algorithm with
+ * every product (A Y, A^T Z, A V, every QR trailing update, Gram matrix and
+ * Q formation) an exact-accumulation product of 8 fixed-point BF16 slices per
+ * operand (every operand row carried to 2^-63 of its scale, slice pairs
+ * s + t < 8, integer drains); Householder panels and T factors in FP64.
+ * Results agree with the FP64 mode to FP64 rounding. */
+#define PURL_MODE_FP64_EMU 4
 
 /* Human-readable text for a status code (static storage). */
 const char *purl_status_str(int status);
@@ -287,10 +294,10 @@ int purl_gemm_f64(char transa, char transb, int m, int n, int k, double alpha, c
 
 /*
  * purl_gemm_tc -- the same product on the BF16 tensor cores (tcgen05, FP32
- * accumulation in tensor memory) with `slices` in {1, 2, 3} ({1..4} when
- * exact): each FP64
+ * accumulation in tensor memory) with `slices` in {1, 2, 3} ({1..4} or 8
+ * when exact): each FP64
  * operand is split into that many BF16 slices and the slice pairs (s, t) with
- * s + t < slices are multiplied (1, 3, 6 or 10 BF16 products).
+ * s + t < slices are multiplied (1, 3, 6, 10 or 36 BF16 products).
  *   exact = 0: floating slices X_0 = bf16(X), X_1 = bf16(X - X_0), ...; the
  *              accumulator's own rounding limits the result to about
  *              (k/16) 2^-23 of sum |a||b| however many slices are used.
@@ -299,7 +306,11 @@ int purl_gemm_f64(char transa, char transb, int m, int n, int k, double alpha, c
  *              most 8 bits) whose products sum without any rounding in the
  *              FP32 accumulator; the tensor memory is drained into
  *              double-FP32 sums every 256 of k.  Error about 2^(-8 slices)
- *              of (row scale) x (column scale) x k.
+ *              of (row scale) x (column scale) x k.  slices = 8 is the FP64
+ *              emulation configuration: chunks of 128 of k drained into
+ *              exact 64-bit integer sums, k <= 2^20 (PURL_ERR_UNSUPPORTED
+ *              beyond), error below 2^-59 of (row max) x (column max) per
+ *              term plus the final FP64 rounding.
  * This is the product engine of the mixed-precision mode.  Operand slices are
  * staged in scratch allocated on `stream`.
  */

@@ -19,6 +19,17 @@
 //
 // Used by the mixed-precision QR (V^T C, the trailing update C - V W, the
 // Gram matrix V^T V, Q formation) and by A V (Section 3, Eq. (6)).
+//
+// Wide configuration (S = 8, FP64 emulation): 8 digits of 8 bits carry every
+// operand row to 2^-63 of its scale.  The 8 classes d = s + t < 8 of a
+// 128-row N tile of 32 columns fill 2 x 8 x 32 = 512 TMEM columns; a class
+// sums at most 8 pairs, so chunks are 128 of K (8 * 128 * 2^14 = 2^24).  All
+// 8 slices of a 64-deep k-block of both operands would take 160 KB of shared
+// memory, so a pipeline stage holds ONE A slice s with the B slices t < 8 - s
+// it meets, and a k-block passes through 8 stages.  The epilogue drains each
+// class as an exact integer into two 64-bit accumulators (classes 0-3 and
+// 4-7, shifted to a common unit); the dropped pairs (s + t >= 8) weigh below
+// 2^-59 of the row and column maxima, so the product is FP64-accurate.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -43,10 +54,12 @@ constexpr int TCX_GROUP = 16;
 // exact, e.g. the Gram matrix of rounded Householder vectors); BN = N tile.
 template <int S, bool ALL, int BN>
 struct TcxCfg {
+  static constexpr bool WIDE = S > 4;  // one A slice per stage, integer drains
   static constexpr int CLASSES = ALL ? 2 * S - 1 : S;
+  static constexpr int KBC = WIDE ? 2 : TCX_KBC;  // k-blocks per exact chunk
   static constexpr int A_BYTES = TC_BM * TC_BK * 2;
   static constexpr int B_BYTES = BN * TC_BK * 2;
-  static constexpr int STAGE_BYTES = S * (A_BYTES + B_BYTES);
+  static constexpr int STAGE_BYTES = WIDE ? A_BYTES + S * B_BYTES : S * (A_BYTES + B_BYTES);
   static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
   static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
@@ -55,6 +68,9 @@ struct TcxCfg {
   static_assert(STAGES >= 2, "stages");
   static_assert(USED_COLS <= 512, "tensor memory");
   static_assert(BN % 32 == 0, "BN");
+  static_assert(!WIDE || (!ALL && S <= 8), "wide: s + t < S classes of at most 8 pairs");
+  static_assert(!WIDE || BN == 32, "wide: N tile of 32");
+  static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -138,18 +154,36 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
       for (long long work = blockIdx.x; work < total && !stop; work += gridDim.x) {
         int m0, n0, kb0, nkb;
         work_geometry(work, m0, n0, kb0, nkb);
-        for (int kb = 0; kb < nkb; ++kb, ++kt) {
-          const int st = (int)(kt % STAGES);
-          const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-          if (!mbar_wait(&empty_bar[st], ph ^ 1u, ctrl, &s_abort)) { stop = true; break; }
-          mbar_arrive_expect_tx(&full_bar[st], (uint32_t)Cfg::STAGE_BYTES);
-          uint8_t *sa = smem + (size_t)st * Cfg::STAGE_BYTES;
-          uint8_t *sb = sa + S * Cfg::A_BYTES;
-          const int kx = kb0 + kb * TC_BK;
+        if constexpr (Cfg::WIDE) {
+          // stage = (k-block kb, A slice s) with B slices t < S - s
+          for (int kb = 0; kb < nkb && !stop; ++kb) {
+            const int kx = kb0 + kb * TC_BK;
+            for (int s = 0; s < S; ++s, ++kt) {
+              const int st = (int)(kt % STAGES);
+              const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+              if (!mbar_wait(&empty_bar[st], ph ^ 1u, ctrl, &s_abort)) { stop = true; break; }
+              mbar_arrive_expect_tx(&full_bar[st], (uint32_t)(Cfg::A_BYTES + (S - s) * Cfg::B_BYTES));
+              uint8_t *sa = smem + (size_t)st * Cfg::STAGE_BYTES;
+              uint8_t *sb = sa + Cfg::A_BYTES;
+              tma_load_3d(sa, &tmA, &full_bar[st], va.r0 + kx, va.c0 + m0, s);
+              for (int t = 0; t < S - s; ++t)
+                tma_load_3d(sb + t * Cfg::B_BYTES, &tmB, &full_bar[st], vb.r0 + kx, vb.c0 + n0, t);
+            }
+          }
+        } else {
+          for (int kb = 0; kb < nkb; ++kb, ++kt) {
+            const int st = (int)(kt % STAGES);
+            const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+            if (!mbar_wait(&empty_bar[st], ph ^ 1u, ctrl, &s_abort)) { stop = true; break; }
+            mbar_arrive_expect_tx(&full_bar[st], (uint32_t)Cfg::STAGE_BYTES);
+            uint8_t *sa = smem + (size_t)st * Cfg::STAGE_BYTES;
+            uint8_t *sb = sa + S * Cfg::A_BYTES;
+            const int kx = kb0 + kb * TC_BK;
 #pragma unroll
-          for (int s = 0; s < S; ++s) tma_load_3d(sa + s * Cfg::A_BYTES, &tmA, &full_bar[st], va.r0 + kx, va.c0 + m0, s);
+            for (int s = 0; s < S; ++s) tma_load_3d(sa + s * Cfg::A_BYTES, &tmA, &full_bar[st], va.r0 + kx, va.c0 + m0, s);
 #pragma unroll
-          for (int s = 0; s < S; ++s) tma_load_3d(sb + s * Cfg::B_BYTES, &tmB, &full_bar[st], vb.r0 + kx, vb.c0 + n0, s);
+            for (int s = 0; s < S; ++s) tma_load_3d(sb + s * Cfg::B_BYTES, &tmB, &full_bar[st], vb.r0 + kx, vb.c0 + n0, s);
+          }
         }
       }
       // never leave the block with copies in flight: the last use of every stage
@@ -165,6 +199,40 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
       for (long long work = blockIdx.x; work < total && !stop; work += gridDim.x) {
         int m0, n0, kb0, nkb;
         work_geometry(work, m0, n0, kb0, nkb);
+        if constexpr (Cfg::WIDE) {
+          for (int kb = 0; kb < nkb && !stop; ++kb) {
+            const int kin = kb % Cfg::KBC, b = (int)(ct & 1);
+            if (kin == 0) {
+              if (!mbar_wait(&tempty_bar[b], ((uint32_t)(ct >> 1) & 1u) ^ 1u, ctrl, &s_abort)) { stop = true; break; }
+              tc_fence_after();
+            }
+            for (int s = 0; s < S; ++s, ++kt) {
+              const int st = (int)(kt % STAGES);
+              const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+              if (!mbar_wait(&full_bar[st], ph, ctrl, &s_abort)) { stop = true; break; }
+              tc_fence_after();
+              const uint32_t sa = smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
+              const uint32_t sb = sa + Cfg::A_BYTES;
+              for (int t = 0; t < S - s; ++t) {
+                const uint32_t dcol = tmem + (uint32_t)((b * Cfg::CLASSES + s + t) * TCX_BN);
+#pragma unroll
+                for (int k = 0; k < TC_BK / 16; ++k) {
+                  const uint64_t ad = sw128_desc(sa + k * 32);
+                  const uint64_t bd = sw128_desc(sb + t * Cfg::B_BYTES + k * 32);
+                  // every class d is first reached at s = 0 (t = d): that product
+                  // opens the chunk's accumulator
+                  tc_mma(dcol, ad, bd, idesc, (kin == 0 && s == 0 && k == 0) ? 0u : 1u);
+                }
+              }
+              tc_commit(&empty_bar[st]);
+            }
+            if (!stop && (kin == Cfg::KBC - 1 || kb == nkb - 1)) {
+              tc_commit(&tfull_bar[b]);
+              ++ct;
+            }
+          }
+          continue;
+        }
         for (int kb = 0; kb < nkb; ++kb, ++kt) {
           const int kin = kb % TCX_KBC, b = (int)(ct & 1);
           if (kin == 0) {
@@ -213,7 +281,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
     for (long long work = blockIdx.x; work < total && ok; work += gridDim.x) {
       int m0, n0, kb0, nkb;
       work_geometry(work, m0, n0, kb0, nkb);
-      const int nch = (nkb + TCX_KBC - 1) / TCX_KBC;
+      const int nch = (nkb + Cfg::KBC - 1) / Cfg::KBC;
       const bool reads_c = (ep.mode == 0 && ep.beta != 0.0);
       const int row = m0 + lane_base + lane;
       if (reads_c && row < M) {
@@ -222,9 +290,16 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
           if (n0 + cbase + j < N)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(ep.C + row + (long long)(n0 + cbase + j) * ep.ldc));
       }
-      float hi[HC], lo[HC];
+      // narrow: one double-FP32 sum of all classes; wide: exact integer sums
+      // H (classes d < S - 4, unit 2^(32 - 8(S-1))) and L (classes d >= S - 4,
+      // unit 2^(-8(S-1))), both relative to one class-0 product
+      constexpr int NA = Cfg::WIDE ? 1 : HC, NW = Cfg::WIDE ? HC : 1;
+      float hi[NA], lo[NA];
+      long long accH[NW], accL[NW];
 #pragma unroll
-      for (int j = 0; j < HC; ++j) hi[j] = lo[j] = 0.0f;
+      for (int j = 0; j < NA; ++j) hi[j] = lo[j] = 0.0f;
+#pragma unroll
+      for (int j = 0; j < NW; ++j) accH[j] = accL[j] = 0;
       for (int c = 0; c < nch; ++c, ++ct) {
         const int b = (int)(ct & 1);
         if (!mbar_wait(&tfull_bar[b], (uint32_t)(ct >> 1) & 1u, ctrl, &s_abort)) {
@@ -236,7 +311,21 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
         for (int d = 0; d < Cfg::CLASSES; ++d) {
           const float w = __int_as_float((127 - 8 * d) << 23);  // 2^(-8d)
           const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)((b * Cfg::CLASSES + d) * TCX_BN + cbase);
-          if constexpr (HC >= 32) {
+          if constexpr (Cfg::WIDE) {
+            // class sums are exact integers below 2^24 in magnitude
+            uint32_t v[16];
+            tmem_ld16(taddr, v);
+            if (d < S - 4) {
+              const int sh = 8 * (S - 5 - d);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) accH[j] += (long long)__float2int_rz(__uint_as_float(v[j])) * (1LL << sh);
+            } else {
+              const int sh = 8 * (S - 1 - d);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) accL[j] += (long long)__float2int_rz(__uint_as_float(v[j])) * (1LL << sh);
+            }
+            (void)w;
+          } else if constexpr (HC >= 32) {
 #pragma unroll
             for (int h = 0; h < HC / 32; ++h) {
               uint32_t v[32];
@@ -278,7 +367,14 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
             const int col = n0 + cbase + j;
             if (col < N) {
               const int k = ea + scB[vb.c0 + col] - 14;
-              const double dh = scaled_float_to_double(hi[j], k), dl = scaled_float_to_double(lo[j], k);
+              double dh, dl;
+              if constexpr (Cfg::WIDE) {
+                dh = int64_scaled_to_double(accH[j], k + 32 - 8 * (S - 1));
+                dl = int64_scaled_to_double(accL[j], k - 8 * (S - 1));
+              } else {
+                dh = scaled_float_to_double(hi[j], k);
+                dl = scaled_float_to_double(lo[j], k);
+              }
               if (ep.mode == 0) {
                 double *p = ep.C + row + (long long)col * ep.ldc;
                 double x;
@@ -428,18 +524,23 @@ int tcx_gemm_view_impl(const Slices &A, int a_r0, int a_c0, const Slices &B, int
   if (M <= 0 || N <= 0) return PURL_OK;
   if (K <= 0 || k_chunk <= 0 || (k_chunk % (TC_BK * TCX_KBC)) != 0 || splits != ceil_div(K, k_chunk))
     return PURL_ERR_UNSUPPORTED;
-  if (S < 1 || S > 4 || A.S < S || B.S < S || !A.scale || !B.scale) return PURL_ERR_UNSUPPORTED;
+  if (S < 1 || (S > 4 && (S != kTcxEmuSlices || all_pairs)) || A.S < S || B.S < S || !A.scale || !B.scale)
+    return PURL_ERR_UNSUPPORTED;
+  // wide sums: |H|, |L| < 2^48.1 per 128-deep chunk; K <= 2^20 keeps both
+  // inside 64 bits
+  if (S > 4 && K > (1 << 20)) return PURL_ERR_UNSUPPORTED;
   if ((a_r0 % 8) != 0 || (b_r0 % 8) != 0) return PURL_ERR_UNSUPPORTED;
   if (ep.mode == 2 && !ep.Pd) return PURL_ERR_UNSUPPORTED;
   if (ep.mode == 0 && !ep.C) return PURL_ERR_UNSUPPORTED;
   if (ep.mode != 0 && ep.mode != 2) return PURL_ERR_UNSUPPORTED;
-  const int BN = all_pairs ? 32 : 64;
+  const int BN = (all_pairs || S > 4) ? 32 : 64;
   CUtensorMap ma, mb;
   PURL_TRY(make_map(&ma, A, a_r0 + K, a_c0 + M, TC_BM));
   PURL_TRY(make_map(&mb, B, b_r0 + K, b_c0 + N, BN));
   TcView va{a_r0, a_c0}, vb{b_r0, b_c0};
 #define PURL_TCX(S_, ALL_, BN_) \
   return launch_tcx<S_, ALL_, BN_>(ma, mb, va, vb, M, N, K, k_chunk, splits, A.scale, B.scale, ep, di->ctrl, s)
+  if (S == kTcxEmuSlices) PURL_TCX(kTcxEmuSlices, false, 32);
   if (!all_pairs) {
     if (S == 1) PURL_TCX(1, false, 64);
     if (S == 2) PURL_TCX(2, false, 64);

@@ -369,14 +369,21 @@ int outer_prepare(int rows, int nbw, const double *FJ, int ldf, int m, int first
   PURL_CUDA_TRY(cudaGetLastError());
   if (!build_t) return PURL_OK;
   PURL_TRY(split_exact(rows, nbw, w.Vo, m, w.Vos, nullptr, s));
-  // exact Gram matrix of the rounded V (all slice pairs)
+  // Gram matrix of the rounded V: exact (all slice pairs) for S <= 4; for the
+  // FP64-emulation slices the pairs s + t >= S weigh below 2^-59, so the
+  // usual product is V^T V^ to FP64 accuracy, as in the FP64 path
   int gs, gch;
   splits_for(nbw, nbw, rows, di->num_sms, &gs, &gch);
   TcEpilogue g;
   g.mode = 2;
   g.Pd = w.Go;
-  g.tag = "tcx outer Gram (all pairs)";
-  PURL_TRY(tcx_gemm_all_pairs(w.Vos, 0, 0, w.Vos, 0, 0, nbw, nbw, rows, w.S, g, gs, gch, s));
+  if (w.S <= 4) {
+    g.tag = "tcx outer Gram (all pairs)";
+    PURL_TRY(tcx_gemm_all_pairs(w.Vos, 0, 0, w.Vos, 0, 0, nbw, nbw, rows, w.S, g, gs, gch, s));
+  } else {
+    g.tag = "tcx outer Gram";
+    PURL_TRY(tcx_gemm_view(w.Vos, 0, 0, w.Vos, 0, 0, nbw, nbw, rows, w.S, g, gs, gch, s));
+  }
   { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "sum_partials_kernel");
     sum_partials_kernel<<<launch_grid((long long)nbw * nbw, 256), 256, 0, s>>>(nbw * nbw, gs, w.Go, w.Tt); }
   PURL_CUDA_TRY(cudaGetLastError());

@@ -55,10 +55,11 @@ __device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
   return (unsigned short)(sgn | ((unsigned)(127 + msb) << 7) | mant);
 }
 
-// Write the S digits of x (|x| < 2^e) as BF16 slices: slice s at dst[s * plane].
+// Write the S digits of x (|x| < 2^e) as BF16 slices: slice s at dst[s * plane],
+// S <= 8 (P = 7 + 8(S-1) <= 63 keeps N in a 64-bit integer).
 __device__ __forceinline__ void write_fixed_slices(double x, int e, __nv_bfloat16 *dst, long long plane, int S) {
   long long n = fixed_point(x, e, 7 + 8 * (S - 1));
-  unsigned short digit[4];
+  unsigned short digit[8];
   for (int s = S - 1; s >= 1; --s) {
     const long long d = ((n + 128) & 255) - 128;
     digit[s] = bf16_bits_of_int((int)d);
@@ -81,6 +82,30 @@ __device__ __forceinline__ double scaled_float_to_double(float f, int k) {
   const unsigned long long e11 = (unsigned long long)(int)(e8 + 896 + k);
   const unsigned long long m = (unsigned long long)(b & 0x7FFFFFu) << 29;
   return __longlong_as_double((long long)(sign | (e11 << 52) | m));
+}
+
+// The FP64 value nearest to x * 2^k (ties away from zero) for |x| < 2^62,
+// assembled with integer operations only; zero for x == 0 and for results
+// below the normal FP64 range.
+__device__ __forceinline__ double int64_scaled_to_double(long long x, int k) {
+  if (x == 0) return 0.0;
+  const unsigned long long sign = x < 0 ? (1ULL << 63) : 0ULL;
+  const unsigned long long a = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+  int msb = 63 - __clzll((long long)a);
+  unsigned long long mant;
+  if (msb <= 52) {
+    mant = a << (52 - msb);
+  } else {
+    const int r = msb - 52;
+    mant = (a + (1ULL << (r - 1))) >> r;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++msb;
+    }
+  }
+  const int E = msb + k + 1023;
+  if (E <= 0) return 0.0;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
 }
 
 }  // namespace purl

@@ -67,8 +67,12 @@ int split_exact(int R, int Cc, const double *X, long long ldx, Slices dst, const
                 cudaStream_t s);
 // Column exponents e_c = exponent of (1 + 2^-20) * ||X(:,c)||_2 (so |X(r,c)| < 2^e_c).
 int column_norm_exponents(int R, int Cc, const double *X, long long ldx, int *e, cudaStream_t s);
+// Slices of the FP64-emulation configuration of the exact engine: 8 digits of
+// 8 bits (every operand row carried to 2^-63 of its scale), pairs s + t < 8.
+constexpr int kTcxEmuSlices = 8;
+
 // D = A B^T (M x N) with exact accumulation over exact slices (A.scale, B.scale
-// required), S = 1..4.  Epilogue mode 0 (FP64 C = alpha D + beta C, optional
+// required), S = 1..4 or kTcxEmuSlices (K <= 2^20).  Epilogue mode 0 (FP64 C = alpha D + beta C, optional
 // slices out) or mode 2 (FP64 split-K partials at Pd + z*M*N).
 int tcx_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0, int b_c0, int M, int N,
                   int K, int S, const TcEpilogue &ep, int splits, int k_chunk, cudaStream_t s);

@@ -57,15 +57,33 @@ constexpr int kFinalSlices = 4;
 struct UrvWork {
   double *buf[3] = {nullptr, nullptr, nullptr};  // each m x n
   QrWork qr;                                     // FP64 mode
-  // mixed mode
+  // mixed and FP64-emulation modes
   QrMixWork qm;
   Slices At1, An1, Ax, Ys, Zs, Vx;
+  Slices Ae, Ze;  // FP64 emulation: A (m x n, scale per column), Z (m x n)
 };
+
+// FP64 emulation: every product, including the power steps, with
+// kTcxEmuSlices exact slices (every operand row carried to 2^-63 of its scale).
+static int urv_plan_emu(Arena &ar, int m, int n, UrvWork *w) {
+  constexpr int S = kTcxEmuSlices;
+  PURL_TRY(qr_mixed_plan(ar, m, n, S, &w->qm));
+  w->Ax = make_slices(ar.take<__nv_bfloat16>(slice_elems(n, m, S)), n, m, S);  // A^T: rows of A as operand rows
+  w->Ax.scale = ar.take<int>(m > 0 ? m : 1);
+  w->Ae = make_slices(ar.take<__nv_bfloat16>(slice_elems(m, n, S)), m, n, S);  // A: columns as operand rows
+  w->Ae.scale = ar.take<int>(n > 0 ? n : 1);
+  w->Ze = make_slices(ar.take<__nv_bfloat16>(slice_elems(m, n, S)), m, n, S);
+  w->Ze.scale = ar.take<int>(n > 0 ? n : 1);
+  w->Vx = make_slices(ar.take<__nv_bfloat16>(slice_elems(n, n, S)), n, n, S);  // Y, then V
+  w->Vx.scale = ar.take<int>(n > 0 ? n : 1);
+  return PURL_OK;
+}
 
 static int urv_plan(Arena &ar, int m, int n, int mode, UrvWork *w) {
   size_t mn = (size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1);
   for (int i = 0; i < 3; ++i) w->buf[i] = ar.take<double>(mn);
   if (mode == PURL_MODE_FP64) return qr_plan(ar, m, n, mode, &w->qr);
+  if (mode == PURL_MODE_FP64_EMU) return urv_plan_emu(ar, m, n, w);
   PURL_TRY(qr_mixed_plan(ar, m, n, kFinalSlices, &w->qm));
   w->At1 = make_slices(ar.take<__nv_bfloat16>(slice_elems(n, m, 1)), n, m, 1);
   w->An1 = make_slices(ar.take<__nv_bfloat16>(slice_elems(m, n, 1)), m, n, 1);
@@ -78,7 +96,9 @@ static int urv_plan(Arena &ar, int m, int n, int mode, UrvWork *w) {
   return PURL_OK;
 }
 
-static bool mode_ok(int mode) { return mode == PURL_MODE_FP64 || mode == PURL_MODE_MIXED_BF16; }
+static bool mode_ok(int mode) {
+  return mode == PURL_MODE_FP64 || mode == PURL_MODE_MIXED_BF16 || mode == PURL_MODE_FP64_EMU;
+}
 
 // Stream-ordered scratch: the caller's workspace, or one allocated on the stream.
 struct Scratch {
@@ -196,11 +216,75 @@ static int urv_run_mixed(int m, int n, const double *A, int lda, int q, int reor
   return qr_sign_fix(m, n, F, m, U, ldu, R, ldr, s);
 }
 
+// FP64 emulated on the tensor cores: the FP64 path's algorithm with every
+// product -- A Y, A^T Z, A V, and the trailing updates and Q formation of
+// every QR -- as an exact-accumulation product of kTcxEmuSlices fixed-point
+// BF16 slices, each operand row carried to 2^-63 of its scale.  Householder
+// panels, their Gram matrices and the T factors stay in FP64.
+static int urv_run_emu(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                       double *U, int ldu, double *R, int ldr, double *V, int ldv, UrvWork &w,
+                       cudaStream_t s) {
+  constexpr int S = kTcxEmuSlices;
+  double *Y = w.buf[0], *Z = w.buf[1], *F = w.buf[2];
+  qr_mixed_use_slices(w.qm, S);
+  // A's slices, made once: A^T (rows of A as operand rows, staged in Z) for
+  // A Y and A V, A itself (columns as operand rows) for A^T Z
+  PURL_TRY(transpose_f64(m, n, A, lda, Z, n, s));
+  PURL_TRY(split_exact(n, m, Z, n, w.Ax, nullptr, s));
+  if (q > 0) PURL_TRY(split_exact(m, n, A, lda, w.Ae, nullptr, s));
+  const int kn = ceil_div(n, 256) * 256, km = ceil_div(m, 256) * 256;
+  TcEpilogue ep;
+  ep.mode = 0;
+  ep.tag = "tcx emu A Y";
+  PURL_TRY(launch_gaussian(seed, 0, n, n, Y, n, s));
+  for (int i = 1; i <= q; ++i) {
+    PURL_TRY(split_exact(n, n, Y, n, w.Vx, nullptr, s));
+    ep.C = F;
+    ep.ldc = m;
+    ep.tag = "tcx emu A Y";
+    PURL_TRY(tcx_gemm_view(w.Ax, 0, 0, w.Vx, 0, 0, m, n, n, S, ep, 1, kn, s));  // F = A Y
+    if (reorth) {
+      PURL_TRY(qr_mixed_factor(m, n, F, m, w.qm, s));
+      PURL_TRY(qr_mixed_form_q(m, n, F, m, w.qm, Z, m, s));
+      PURL_TRY(qr_sign_fix(m, n, F, m, Z, m, nullptr, 0, s));
+    } else {
+      double *t = F; F = Z; Z = t;
+    }
+    PURL_TRY(split_exact(m, n, Z, m, w.Ze, nullptr, s));
+    ep.C = F;
+    ep.ldc = n;
+    ep.tag = "tcx emu A^T Z";
+    PURL_TRY(tcx_gemm_view(w.Ae, 0, 0, w.Ze, 0, 0, n, n, m, S, ep, 1, km, s));  // F = A^T Z
+    if (reorth && i < q) {
+      PURL_TRY(qr_mixed_factor(n, n, F, n, w.qm, s));
+      PURL_TRY(qr_mixed_form_q(n, n, F, n, w.qm, Y, n, s));
+      PURL_TRY(qr_sign_fix(n, n, F, n, Y, n, nullptr, 0, s));
+    } else {
+      double *t = F; F = Y; Y = t;
+    }
+  }
+  // Eq. (5): (A^T A)^q G = V Z'
+  PURL_TRY(qr_mixed_factor(n, n, Y, n, w.qm, s));
+  PURL_TRY(qr_mixed_form_q(n, n, Y, n, w.qm, V, ldv, s));
+  PURL_TRY(qr_sign_fix(n, n, Y, n, V, ldv, nullptr, 0, s));
+  // A V, then Eq. (6): A V = U R
+  PURL_TRY(split_exact(n, n, V, ldv, w.Vx, nullptr, s));
+  ep.C = F;
+  ep.ldc = m;
+  ep.tag = "tcx emu A V";
+  PURL_TRY(tcx_gemm_view(w.Ax, 0, 0, w.Vx, 0, 0, m, n, n, S, ep, 1, kn, s));
+  PURL_TRY(qr_mixed_factor(m, n, F, m, w.qm, s));
+  PURL_TRY(qr_mixed_form_q(m, n, F, m, w.qm, U, ldu, s));
+  return qr_sign_fix(m, n, F, m, U, ldu, R, ldr, s);
+}
+
 static int urv_run(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
                    double *U, int ldu, double *R, int ldr, double *V, int ldv, int mode,
                    UrvWork &w, cudaStream_t s) {
   if (mode == PURL_MODE_MIXED_BF16)
     return urv_run_mixed(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, w, s);
+  if (mode == PURL_MODE_FP64_EMU)
+    return urv_run_emu(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, w, s);
   return urv_run_fp64(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, w, s);
 }
 
@@ -347,7 +431,7 @@ size_t purl_qr_workspace_bytes(int m, int n, int mode) {
     if (qr_plan(ar, m, n, mode, &w) != PURL_OK) return 0;
   } else {
     QrMixWork w;
-    if (qr_mixed_plan(ar, m, n, kFinalSlices, &w) != PURL_OK) return 0;
+    if (qr_mixed_plan(ar, m, n, mode == PURL_MODE_FP64_EMU ? kTcxEmuSlices : kFinalSlices, &w) != PURL_OK) return 0;
   }
   return ar.used;
 }
@@ -379,7 +463,7 @@ int purl_qr(int m, int n, const double *M, int ldm, double *Q, int ldq, double *
     return qr_explicit(m, n, F, m, Q, ldq, R, ldr, mode, w, stream);
   }
   QrMixWork w;
-  PURL_TRY(qr_mixed_plan(ar, m, n, kFinalSlices, &w));
+  PURL_TRY(qr_mixed_plan(ar, m, n, mode == PURL_MODE_FP64_EMU ? kTcxEmuSlices : kFinalSlices, &w));
   if (!ar.ok) return PURL_ERR_NOMEM;
   PURL_TRY(copy_matrix(m, n, M, ldm, F, m, stream));
   PURL_TRY(qr_mixed_factor(m, n, F, m, w, stream));
@@ -423,7 +507,8 @@ int purl_gemm_tc(char transa, char transb, int m, int n, int k, double alpha, co
   if (ldb < (brows > 1 ? brows : 1)) return -10;
   if (!C && (long long)m * n > 0) return -12;
   if (ldc < (m > 1 ? m : 1)) return -13;
-  if (slices < 1 || slices > (exact ? 4 : 3)) return -14;
+  if (slices < 1 || (exact ? (slices > 4 && slices != kTcxEmuSlices) : slices > 3)) return -14;
+  if (exact && slices > 4 && k > (1 << 20)) return PURL_ERR_UNSUPPORTED;
   if ((long long)m * n == 0) return PURL_OK;
   if (!device_info()) return PURL_ERR_CUDA;
   if (k == 0) return gemm_f64(false, false, m, n, 0, 0.0, A, lda, B, ldb, beta, C, ldc, stream);

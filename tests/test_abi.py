@@ -60,6 +60,10 @@ def test_argument_errors_are_reported_before_device_work(purl):
     assert L.purl_urv_factor(4, 4, fake, 4, -2, 1, 7, fake, 4, fake, 4, fake, 4, nul) == -5
     assert L.purl_urv_factor(4, 4, fake, 4, 1, 1, 7, fake, 4, fake, 3, fake, 4, nul) == -11
     assert L.purl_urv_factor_ex(4, 4, fake, 4, 1, 1, 7, fake, 4, fake, 4, fake, 4, 99, nul, 0, nul) == -14
+    assert L.purl_urv_factor_ex(4, 4, fake, 4, 1, 1, 7, fake, 4, fake, 4, fake, 4, 3, nul, 0, nul) == -14
+    # exact slices: 1..4 or the FP64-emulation configuration (8); floating slices: 1..3
+    for slices, exact in ((5, 1), (6, 1), (7, 1), (9, 1), (4, 0), (8, 0), (0, 1)):
+        assert L.purl_gemm_tc(b"N", b"N", 1, 1, 1, 1.0, fake, 1, fake, 1, 0.0, fake, 1, slices, exact, nul) == -14
     assert L.purl_gemm_f64(b"X", b"N", 1, 1, 1, 1.0, fake, 1, fake, 1, 0.0, fake, 1, nul) == -1
     assert L.purl_urv_truncate(4, 4, 5, fake, 4, fake, 4, fake, 4, fake, 4, nul) == -3
     assert L.purl_qr(2, 3, fake, 2, fake, 2, fake, 3, 0, nul, 0, nul) == purl.PURL_ERR_SHAPE
