@@ -41,6 +41,33 @@ def sigma_profile(kind: str, n: int, decades: float = 8.0, power: float = 2.0,
     raise ValueError(f"unknown sigma profile {kind!r}")
 
 
+# Matrices 1-3 of the paper's numerical section (200 x 160, Haar factors).
+QUALITY_M, QUALITY_N = 200, 160
+QUALITY_SEED_U, QUALITY_SEED_V = 71, 72
+
+
+def quality_sigma(name: str, n: int = QUALITY_N) -> np.ndarray:
+    """Singular values of the paper's test matrices (Section 7), with these readings:
+    "fast": Matrix 1, printed as (1e-20)^(k-1), which underflows after k ~ 16; read as
+            10^(-20 (k-1)/(n-1)), twenty decades over the n values;
+    "slow": Matrix 2, 1/k;
+    "s":    Matrix 3, 10^-(1 + tanh(5(-1 + 2k/n))) for k <= 80 with n = 160, and 10^-2 for every
+            k > 80 (the text gives 81..150 only)."""
+    k = np.arange(1, n + 1, dtype=np.float64)
+    if name == "fast":
+        return 10.0 ** (-20.0 * (k - 1) / max(n - 1, 1))
+    if name == "slow":
+        return 1.0 / k
+    if name == "s":
+        return np.where(k <= 80, 10.0 ** (-(1.0 + np.tanh(5.0 * (-1.0 + 2.0 * k / n)))), 1e-2)
+    raise ValueError(f"unknown test matrix {name!r}")
+
+
+def quality_matrix_np(name: str) -> np.ndarray:
+    """Matrix 1, 2 or 3 ("fast", "slow", "s"): Uh diag(sigma) Vh^T, 200 x 160."""
+    return test_matrix_np(QUALITY_M, QUALITY_N, quality_sigma(name, QUALITY_N), QUALITY_SEED_U, QUALITY_SEED_V)
+
+
 def haar_np(rows: int, cols: int, seed: int) -> np.ndarray:
     """rows x cols matrix with Haar-distributed orthonormal columns (rows >= cols)."""
     X = np.random.default_rng(seed).standard_normal((rows, cols))
