@@ -416,7 +416,9 @@ def end_to_end(a, A, U, R, V, ws, mode, seed, world, dev, B):
         with torch.cuda.stream(h2d):
             h2d.wait_event(a_free[b])
             mk[0].record(h2d)
-            dA[b].copy_(hA, non_blocking=True)
+            # column-major m x n is a contiguous n x m row-major array: copying the
+            # contiguous bases makes each copy one straight DMA of pinned memory
+            dA[b].t().copy_(hA.t(), non_blocking=True)
             mk[1].record(h2d)
             a_ready[b].record(h2d)
 
@@ -432,9 +434,9 @@ def end_to_end(a, A, U, R, V, ws, mode, seed, world, dev, B):
         with torch.cuda.stream(d2h):
             d2h.wait_event(done[b])
             mk[2].record(d2h)
-            hU.copy_(Ub, non_blocking=True)
-            hR.copy_(Rb, non_blocking=True)
-            hV.copy_(Vb, non_blocking=True)
+            hU.t().copy_(Ub.t(), non_blocking=True)
+            hR.t().copy_(Rb.t(), non_blocking=True)
+            hV.t().copy_(Vb.t(), non_blocking=True)
             mk[3].record(d2h)
             out_free[b].record(d2h)
 
