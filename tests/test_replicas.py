@@ -62,3 +62,29 @@ def test_flop_count_matches_table_1_reading():
     # GEMM term 2(2q+1) m n^2 (Table 1 read with mn^2), no reorth: 2 QRs
     m = 3 * n
     assert bench.urv_flops(m, n, 1, False) == pytest.approx(6 * m * n * n + bench.qr_flops(n, n) + bench.qr_flops(m, n))
+
+
+def test_roofline_picks_the_dominant_kernel_and_its_peak():
+    import bench
+    peaks, _ = bench._peaks()
+    steps = 2
+    named = {
+        "tcx outer update": {"launches": 10, "ms": 500.0, "flops": 2.0e14, "bytes": 1e12},
+        "panel_kernel": {"launches": 100, "ms": 300.0, "flops": 2.0e10, "bytes": 1e9},
+        "split_exact_kernel": {"launches": 50, "ms": 100.0, "flops": 0.0, "bytes": 3e11},
+    }
+    r = bench.roofline(None, named, steps, "mixed")
+    assert r["kernel"] == "tcx outer update" and r["bound"] == "tensor"
+    assert r["achieved"] == pytest.approx(2.0e14 / 0.5 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / peaks.get("bf16_tflops_sustained", 1700.0))
+    assert r["launches_per_step"] == 5 and r["avg_launch_ms"] == pytest.approx(50.0)
+    # FP64 kernels against the DFMA peak, everything else against the copy bandwidth
+    named["tcx outer update"]["ms"] = 1.0
+    r = bench.roofline(None, named, steps, "mixed")
+    assert r["kernel"] == "panel_kernel" and r["bound"] == "alu"
+    assert r["frac"] == pytest.approx(2.0e10 / 0.3 / 1e12 / bench.FP64_DFMA_PEAK_TFLOPS)
+    named["panel_kernel"]["ms"] = 1.0
+    r = bench.roofline(None, named, steps, "mixed")
+    assert r["kernel"] == "split_exact_kernel" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(3e11 / 0.1 / 1e9)
+    assert bench.roofline(None, {}, steps, "mixed") is None
