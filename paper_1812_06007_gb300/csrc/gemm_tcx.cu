@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
         const bool plain = (ep.alpha == 1.0 && ep.beta == 0.0);
         const bool subtract = (ep.alpha == -1.0 && ep.beta == 1.0);
         const int z = (int)(work / tiles);
-        constexpr int BATCH = 8;  // independent loads of C kept in flight
+        constexpr int BATCH = Cfg::WIDE ? 8 : 16;  // independent loads of C kept in flight
 #pragma unroll
         for (int j0 = 0; j0 < HC; j0 += BATCH) {
           double cv[BATCH];
