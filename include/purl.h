@@ -62,7 +62,10 @@ extern "C" {
  * Q formation) an exact-accumulation product of 8 fixed-point BF16 slices per
  * operand (every operand row carried to 2^-63 of its scale, slice pairs
  * s + t < 8, integer drains); Householder panels and T factors in FP64.
- * Results agree with the FP64 mode to FP64 rounding. */
+ * Results agree with the FP64 mode to FP64 rounding.  Every product reduces
+ * over at most 2^20 rows: m <= 2^20 for purl_urv_factor_ex and purl_qr,
+ * n <= 2^20 for purl_ulv_factor_ex, else PURL_ERR_UNSUPPORTED (workspace
+ * queries return 0). */
 #define PURL_MODE_FP64_EMU 4
 
 /* Human-readable text for a status code (static storage). */

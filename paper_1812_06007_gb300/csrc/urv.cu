@@ -100,6 +100,11 @@ static bool mode_ok(int mode) {
   return mode == PURL_MODE_FP64 || mode == PURL_MODE_MIXED_BF16 || mode == PURL_MODE_FP64_EMU;
 }
 
+// The FP64-emulation products reduce over at most 2^20 rows (their 64-bit
+// drains); a factorization with more rows is refused before any allocation.
+constexpr int kEmuMaxRows = 1 << 20;
+static bool emu_rows_ok(int mode, int rows) { return mode != PURL_MODE_FP64_EMU || rows <= kEmuMaxRows; }
+
 // Stream-ordered scratch: the caller's workspace, or one allocated on the stream.
 struct Scratch {
   void *ptr = nullptr;
@@ -327,7 +332,7 @@ const char *purl_status_str(int status) {
 const char *purl_version(void) { return "purl 0.1.0 sm_103a"; }
 
 size_t purl_urv_workspace_bytes(int m, int n, int mode) {
-  if (m < 0 || n < 0 || m < n || !mode_ok(mode)) return 0;
+  if (m < 0 || n < 0 || m < n || !mode_ok(mode) || !emu_rows_ok(mode, m)) return 0;
   Arena ar;
   UrvWork w;
   if (urv_plan(ar, m, n, mode, &w) != PURL_OK) return 0;
@@ -340,6 +345,7 @@ int purl_urv_factor_ex(int m, int n, const double *A, int lda, int q, int reorth
   int st = check_factor_args(m, n, A, lda, q, U, ldu, R, ldr, V, ldv);
   if (st != PURL_OK) return st;
   if (!mode_ok(mode)) return -14;
+  if (!emu_rows_ok(mode, m)) return PURL_ERR_UNSUPPORTED;
   if (n == 0) return PURL_OK;
   if (!device_info()) return PURL_ERR_CUDA;
   size_t need = purl_urv_workspace_bytes(m, n, mode);
@@ -371,7 +377,7 @@ static int ulv_plan(Arena &ar, int m, int n, int mode, double **At, double **Rt,
 }
 
 size_t purl_ulv_workspace_bytes(int m, int n, int mode) {
-  if (m < 0 || n < 0 || m > n || !mode_ok(mode)) return 0;
+  if (m < 0 || n < 0 || m > n || !mode_ok(mode) || !emu_rows_ok(mode, n)) return 0;
   Arena ar;
   double *At, *Rt;
   UrvWork w;
@@ -395,6 +401,7 @@ int purl_ulv_factor_ex(int m, int n, const double *A, int lda, int q, int reorth
   if (!V && (long long)m * n > 0) return -12;
   if (ldv < (n > 1 ? n : 1)) return -13;
   if (!mode_ok(mode)) return -14;
+  if (!emu_rows_ok(mode, n)) return PURL_ERR_UNSUPPORTED;
   if (m == 0) return PURL_OK;
   if (!device_info()) return PURL_ERR_CUDA;
   const size_t need = purl_ulv_workspace_bytes(m, n, mode);
@@ -422,7 +429,7 @@ int purl_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double 
 }
 
 size_t purl_qr_workspace_bytes(int m, int n, int mode) {
-  if (m < 0 || n < 0 || m < n || !mode_ok(mode)) return 0;
+  if (m < 0 || n < 0 || m < n || !mode_ok(mode) || !emu_rows_ok(mode, m)) return 0;
   Arena ar;
   double *F = ar.take<double>((size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1));
   (void)F;
@@ -446,6 +453,7 @@ int purl_qr(int m, int n, const double *M, int ldm, double *Q, int ldq, double *
   if (Q && ldq < (m > 1 ? m : 1)) return -6;
   if (R && ldr < (n > 1 ? n : 1)) return -8;
   if (!mode_ok(mode)) return -9;
+  if (!emu_rows_ok(mode, m)) return PURL_ERR_UNSUPPORTED;
   if (n == 0) return PURL_OK;
   if (!device_info()) return PURL_ERR_CUDA;
   size_t need = purl_qr_workspace_bytes(m, n, mode);

@@ -61,6 +61,16 @@ def test_argument_errors_are_reported_before_device_work(purl):
     assert L.purl_urv_factor(4, 4, fake, 4, 1, 1, 7, fake, 4, fake, 3, fake, 4, nul) == -11
     assert L.purl_urv_factor_ex(4, 4, fake, 4, 1, 1, 7, fake, 4, fake, 4, fake, 4, 99, nul, 0, nul) == -14
     assert L.purl_urv_factor_ex(4, 4, fake, 4, 1, 1, 7, fake, 4, fake, 4, fake, 4, 3, nul, 0, nul) == -14
+    # the FP64-emulation mode reduces over at most 2^20 rows: refused before any device work
+    big = (1 << 20) + 1
+    assert L.purl_urv_factor_ex(big, 4, fake, big, 1, 1, 7, fake, big, fake, 4, fake, 4, 4, nul, 0, nul) == \
+        purl.PURL_ERR_UNSUPPORTED
+    assert L.purl_urv_workspace_bytes(big, 4, 4) == 0
+    assert L.purl_ulv_factor_ex(4, big, fake, 4, 1, 1, 7, fake, 4, fake, 4, fake, big, 4, nul, 0, nul) == \
+        purl.PURL_ERR_UNSUPPORTED
+    assert L.purl_qr(big, 4, fake, big, fake, big, fake, 4, 4, nul, 0, nul) == purl.PURL_ERR_UNSUPPORTED
+    assert L.purl_gemm_tc(b"N", b"N", 1, 1, big, 1.0, fake, 1, fake, big, 0.0, fake, 1, 8, 1, nul) == \
+        purl.PURL_ERR_UNSUPPORTED
     # exact slices: 1..4 or the FP64-emulation configuration (8); floating slices: 1..3
     for slices, exact in ((5, 1), (6, 1), (7, 1), (9, 1), (4, 0), (8, 0), (0, 1)):
         assert L.purl_gemm_tc(b"N", b"N", 1, 1, 1, 1.0, fake, 1, fake, 1, 0.0, fake, 1, slices, exact, nul) == -14
