@@ -26,6 +26,13 @@
  *   - Argument errors return -i for the i-th argument (LAPACK style, counting
  *     from 1), PURL_ERR_SHAPE when m < n (factor A^T instead: Section 1 notes
  *     that a URV of A^T gives a ULV of A and vice versa).
+ *   - Non-finite input: every entry point that takes A (factor, ULV, QR,
+ *     RSVD, backward) scans it on the device first.  If any entry is NaN or
+ *     infinite, PURL_ERR_NONFINITE is recorded in the device status word
+ *     (purl_device_status) and every output of the call is overwritten with
+ *     NaN, in every mode (the tensor-core modes' fixed-point slicing would
+ *     otherwise turn such an entry into finite but meaningless results).  The
+ *     scan reads A once (8 m n bytes).
  *   - Every routine is deterministic: the same inputs on the same GPU give the
  *     same bits.
  */
@@ -43,7 +50,7 @@ extern "C" {
 /* status codes */
 #define PURL_OK 0
 #define PURL_ERR_SHAPE (-100)  /* m < n */
-#define PURL_ERR_NONFINITE 1   /* reserved: non-finite input detected */
+#define PURL_ERR_NONFINITE 1   /* A held a NaN or an infinity (device status word) */
 #define PURL_ERR_TIMEOUT 2     /* a bounded device-side wait ran out */
 #define PURL_ERR_CUDA 3        /* a CUDA runtime call failed */
 #define PURL_ERR_NOMEM 4       /* workspace allocation failed or too small */
@@ -262,6 +269,16 @@ int purl_gaussian_f32(uint64_t seed, uint64_t stream_id, int rows, int cols, flo
 int purl_wait_probe(int blocks, int missing, long long polls, cudaStream_t stream);
 
 /*
+ * purl_wait_probe_noalloc -- the same probe, reporting to the status word that
+ * purl_gemm_tc_noalloc keeps in its static device array (setting that array up
+ * on this device as the entry point's first call does, which synchronises the
+ * device).  Shows that a bounded wait running out inside the allocation-free
+ * entry point reaches purl_device_status.  Arguments and errors as
+ * purl_wait_probe.
+ */
+int purl_wait_probe_noalloc(int blocks, int missing, long long polls, cudaStream_t stream);
+
+/*
  * purl_gaussian -- the Gaussian matrix G of Section 3 (the paper fixes no
  * generator; this library's is defined here).  Element e of the rows x cols
  * matrix, e = i + j*rows (column-major linear index), is word e%4 of the
@@ -343,6 +360,9 @@ int purl_gemm_tc(char transa, char transb, int m, int n, int k, double alpha, co
  *   - Every call reuses the same array, which keeps the last call's
  *     contents.  Calls that overlap on the GPU (different streams, or host
  *     threads racing) race on it: serialise them, e.g. on one stream.
+ *   - Device-side errors (a bounded wait that ran out) go to a status word at
+ *     the start of the array; purl_device_status reads and clears it together
+ *     with the library's own word.
  * Arguments, results and return codes are those of purl_gemm_tc with exact = 0.
  */
 int purl_gemm_tc_noalloc(char transa, char transb, int m, int n, int k, double alpha, const double *A,
@@ -360,9 +380,11 @@ int purl_urv_reconstruct(int m, int n, const double *U, int ldu, const double *R
                          const double *V, int ldv, double *Ak, int ldak, cudaStream_t stream);
 
 /*
- * purl_device_status -- read and clear the current device's status word
- * (PURL_OK or the first device-side error since the last call).  Synchronises
- * `stream`.
+ * purl_device_status -- read and clear the current device's status words
+ * (PURL_OK or the first device-side error since the last call): the
+ * library's per-device word and, once purl_gemm_tc_noalloc has been set up on
+ * the device, the word in that entry point's static array (the library's
+ * word is reported first when both are set).  Synchronises `stream`.
  */
 int purl_device_status(cudaStream_t stream);
 

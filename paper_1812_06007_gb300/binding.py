@@ -59,6 +59,7 @@ SIGNATURES = {
     "purl_urv_reconstruct": (_i, [_i, _i, _p, _i, _p, _i, _p, _i, _p, _i, _p]),
     "purl_device_status": (_i, [_p]),
     "purl_wait_probe": (_i, [_i, _i, ctypes.c_longlong, _p]),
+    "purl_wait_probe_noalloc": (_i, [_i, _i, ctypes.c_longlong, _p]),
     "purl_launch_count": (ctypes.c_ulonglong, []),
     "purl_profile_enable": (None, [_i]),
     "purl_profile_reset": (None, []),
@@ -379,6 +380,11 @@ def purl_urv_reconstruct(U, R, V, out=None, stream=None):
 
 def purl_wait_probe(blocks: int, missing: bool, polls: int, stream=None):
     _check("purl_wait_probe", lib().purl_wait_probe(blocks, int(bool(missing)), polls, _stream(stream)))
+
+
+def purl_wait_probe_noalloc(blocks: int, missing: bool, polls: int, stream=None):
+    _check("purl_wait_probe_noalloc",
+           lib().purl_wait_probe_noalloc(blocks, int(bool(missing)), polls, _stream(stream)))
 
 
 def purl_device_status(stream=None) -> int:

@@ -157,12 +157,14 @@ struct BwdPlan {
   double *F = nullptr;      // m x n scratch for factorizations and products
   double *Cb = nullptr, *Vb = nullptr, *Wb = nullptr, *Pb = nullptr, *Yb = nullptr;
   double *Rbu = nullptr;    // upper triangle of Rbar
+  int *finite = nullptr;    // non-finite input flag
   AdjWork aw;
   QrWork qw;
 };
 
 int bwd_plan(Arena &ar, int m, int n, int q, BwdPlan *p) {
   const size_t nn = (size_t)n * n, mn = (size_t)m * n;
+  p->finite = ar.take<int>(1);
   p->Yprev = ar.take<double>(nn * (q + 1));
   p->Z = ar.take<double>(mn * (q > 0 ? q : 1));
   p->S = ar.take<double>(nn * (q > 0 ? q : 1));
@@ -282,8 +284,10 @@ int purl_urv_backward(int m, int n, const double *A, int lda, int q, int reorth,
   BwdPlan p;
   int st = bwd_plan(ar, m, n, q, &p);
   if (st == PURL_OK && !ar.ok) st = PURL_ERR_NOMEM;
+  if (st == PURL_OK) st = finite_check(m, n, A, lda, p.finite, stream);
   if (st == PURL_OK)
     st = urv_backward_run(m, n, A, lda, q, reorth, seed, Ubar, ldub, Rbar, ldrb, Vbar, ldvb, Abar, ldab, p, stream);
+  if (st == PURL_OK) st = finite_poison(p.finite, m, n, Abar, ldab, stream);
   if (owned) cudaFreeAsync(ptr, stream);
   return st;
 }

@@ -41,6 +41,19 @@ struct DeviceInfo {
 // CUDA failure.
 const DeviceInfo *device_info();
 
+// The allocation-free product entry point keeps its own status word in its
+// static device array: read and clear it (PURL_OK when never set up), and get
+// its device address (setting the array up on first use).
+int noalloc_take_status(int *status);
+int noalloc_control(DeviceControl **ctrl);
+
+// Non-finite input: finite_check zeroes *flag (device int), scans the m x n
+// matrix and, if any entry is NaN or infinite, sets *flag and records
+// PURL_ERR_NONFINITE in the device status word; finite_poison overwrites the
+// m x n matrix X with NaN when *flag is set (one tiny launch otherwise).
+int finite_check(int m, int n, const double *A, long long lda, int *flag, cudaStream_t s);
+int finite_poison(const int *flag, int m, int n, double *X, long long ldx, cudaStream_t s);
+
 // Spin budget of a device-side wait: number of polls before giving up
 // (each poll is an L2 round trip of ~0.5-1 us, so this is several seconds).
 constexpr long long kSpinLimit = 1LL << 23;

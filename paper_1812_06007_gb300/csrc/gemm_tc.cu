@@ -375,16 +375,17 @@ __global__ void noalloc_scale_kernel(int m, int n, double beta, double *C, long 
   }
 }
 
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_devs[64];
+
 // Once per device, with that device current: resolve the array's device
 // address (the host-side symbol is not a device pointer) and clear the
 // status word kept at its start.
 int noalloc_setup(NoAllocDevice **out) {
-  static std::mutex mu;
-  static NoAllocDevice devs[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PURL_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(mu);
-  NoAllocDevice &d = devs[dev];
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocDevice &d = g_noalloc_devs[dev];
   if (!d.ready) {
     void *ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return PURL_ERR_CUDA;
@@ -407,6 +408,9 @@ int noalloc_launch(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, i
   long long tiles = (long long)ceil_div(M, TC_BM) * ceil_div(N, BN);
   if (tiles > 0x7fffffffLL) return PURL_ERR_UNSUPPORTED;
   TcView v0{0, 0};
+  LaunchScope ls(KC_GEMM_TC, s, 2.0 * M * (double)N * K * (S * (S + 1) / 2),
+                 (double)S * 2.0 * ((double)M * K + (double)N * K) + 8.0 * M * N * (ep.beta != 0.0 ? 2 : 1),
+                 "tc noalloc");
   tc_gemm_kernel<BN, S><<<dim3((unsigned)tiles, 1), TC_THREADS, Cfg::SMEM, s>>>(ma, mb, v0, v0, M, N, K,
                                                                                  ceil_div(K, TC_BK) * TC_BK, ep, ctrl);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
@@ -448,6 +452,7 @@ extern "C" int purl_gemm_tc_noalloc(char transa, char transb, int m, int n, int 
   if (k == 0) {
     long long g = ((long long)m * n + 255) / 256;
     if (g > (long long)sms * 16) g = (long long)sms * 16;
+    LaunchScope ls(KC_OTHER, stream, 0.0, 16.0 * m * n, "tc noalloc scale");
     noalloc_scale_kernel<<<(int)g, 256, 0, stream>>>(m, n, beta, C, ldc);
     return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
   }
@@ -459,10 +464,12 @@ extern "C" int purl_gemm_tc_noalloc(char transa, char transb, int m, int n, int 
     if (transposed) {
       dim3 grid(ceil_div(R, 32), ceil_div(Cc, 32));
       if (grid.y > 65535) return PURL_ERR_UNSUPPORTED;
+      LaunchScope ls(KC_SPLIT, stream, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc, "tc noalloc split");
       split_t_kernel<<<grid, dim3(32, 8), 0, stream>>>(R, Cc, X, ldx, dst);
     } else {
       long long g = ((long long)R * Cc + 255) / 256;
       if (g > (long long)sms * 16) g = (long long)sms * 16;
+      LaunchScope ls(KC_SPLIT, stream, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc, "tc noalloc split");
       split_kernel<<<(int)g, 256, 0, stream>>>(R, Cc, X, ldx, dst);
     }
     return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
@@ -492,5 +499,38 @@ extern "C" int purl_gemm_tc_noalloc(char transa, char transb, int m, int n, int 
 }
 
 namespace purl {
+
+// Status word of the no-alloc entry point on the current device: read it and
+// clear it (with the abort flag).  *status is PURL_OK when the entry point was
+// never set up on this device.  Called by purl_device_status, so a bounded
+// wait that ran out inside purl_gemm_tc_noalloc is reported like any other.
+int noalloc_take_status(int *status) {
+  *status = PURL_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PURL_ERR_CUDA;
+  unsigned char *scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_devs[dev].ready) return PURL_OK;
+    scratch = g_noalloc_devs[dev].scratch;
+  }
+  DeviceControl h{};
+  if (cudaMemcpy(&h, scratch, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return PURL_ERR_CUDA;
+  if (h.status != PURL_OK || h.abort != 0) {
+    const DeviceControl z{};
+    if (cudaMemcpy(scratch, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return PURL_ERR_CUDA;
+  }
+  *status = h.status;
+  return PURL_OK;
+}
+
+// The no-alloc entry point's status word on the current device (set up like
+// its first call), for the failure-detection probe.
+int noalloc_control(DeviceControl **ctrl) {
+  NoAllocDevice *nd = nullptr;
+  PURL_TRY(noalloc_setup(&nd));
+  *ctrl = reinterpret_cast<DeviceControl *>(nd->scratch);
+  return PURL_OK;
+}
 
 }  // namespace purl

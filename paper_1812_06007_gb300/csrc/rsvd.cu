@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(256) sign_pairs_kernel(int m, int n, double *U
 struct RsvdPlan {
   double *X, *P, *Q, *Bt, *Q2, *R2, *M, *Vr, *sig, *Ws, *Vs, *F;
   int *sweeps;
+  int *finite;       // non-finite input flag
   unsigned *jcount;  // grid-barrier counter, then one rotation count per sweep
   QrWork qw;
 };
@@ -193,6 +194,7 @@ int rsvd_plan(Arena &ar, int m, int n, int l, RsvdPlan *p) {
   p->Vs = ar.take<double>(ll);
   p->F = ar.take<double>((size_t)(m > n ? m : n) * l);
   p->sweeps = ar.take<int>(1);
+  p->finite = ar.take<int>(1);
   p->jcount = ar.take<unsigned>(1 + kMaxSweeps);
   return qr_plan(ar, m > n ? m : n, l, PURL_MODE_FP64, &p->qw);
 }
@@ -289,7 +291,11 @@ int purl_rsvd(int m, int n, const double *A, int lda, int l, int q, int reorth, 
   RsvdPlan p;
   int st = rsvd_plan(ar, m, n, l, &p);
   if (st == PURL_OK && !ar.ok) st = PURL_ERR_NOMEM;
+  if (st == PURL_OK) st = finite_check(m, n, A, lda, p.finite, stream);
   if (st == PURL_OK) st = rsvd_run(m, n, A, lda, l, q, reorth, seed, U, ldu, S, V, ldv, p, stream);
+  if (st == PURL_OK) st = finite_poison(p.finite, m, l, U, ldu, stream);
+  if (st == PURL_OK) st = finite_poison(p.finite, l, 1, S, l, stream);
+  if (st == PURL_OK) st = finite_poison(p.finite, n, l, V, ldv, stream);
   if (owned) cudaFreeAsync(ptr, stream);
   return st;
 }

@@ -55,6 +55,7 @@ constexpr int kReorthSlices = 2;
 constexpr int kFinalSlices = 4;
 
 struct UrvWork {
+  int *finite = nullptr;                         // non-finite input flag
   double *buf[3] = {nullptr, nullptr, nullptr};  // each m x n
   QrWork qr;                                     // FP64 mode
   // mixed and FP64-emulation modes
@@ -81,6 +82,7 @@ static int urv_plan_emu(Arena &ar, int m, int n, UrvWork *w) {
 
 static int urv_plan(Arena &ar, int m, int n, int mode, UrvWork *w) {
   size_t mn = (size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1);
+  w->finite = ar.take<int>(1);
   for (int i = 0; i < 3; ++i) w->buf[i] = ar.take<double>(mn);
   if (mode == PURL_MODE_FP64) return qr_plan(ar, m, n, mode, &w->qr);
   if (mode == PURL_MODE_FP64_EMU) return urv_plan_emu(ar, m, n, w);
@@ -357,7 +359,11 @@ int purl_urv_factor_ex(int m, int n, const double *A, int lda, int q, int reorth
   UrvWork w;
   PURL_TRY(urv_plan(ar, m, n, mode, &w));
   if (!ar.ok) return PURL_ERR_NOMEM;
-  return urv_run(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, mode, w, stream);
+  PURL_TRY(finite_check(m, n, A, lda, w.finite, stream));
+  PURL_TRY(urv_run(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, mode, w, stream));
+  PURL_TRY(finite_poison(w.finite, m, n, U, ldu, stream));
+  PURL_TRY(finite_poison(w.finite, n, n, R, ldr, stream));
+  return finite_poison(w.finite, n, n, V, ldv, stream);
 }
 
 int purl_urv_factor(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
@@ -414,9 +420,13 @@ int purl_ulv_factor_ex(int m, int n, const double *A, int lda, int q, int reorth
   UrvWork w;
   PURL_TRY(ulv_plan(ar, m, n, mode, &At, &Rt, &w));
   if (!ar.ok) return PURL_ERR_NOMEM;
+  PURL_TRY(finite_check(m, n, A, lda, w.finite, stream));
   PURL_TRY(transpose_f64(m, n, A, lda, At, n, stream));                                   // A^T, n x m
   PURL_TRY(urv_run(n, m, At, n, q, reorth, seed, V, ldv, Rt, m, U, ldu, mode, w, stream));  // A^T = V R' U^T
-  return transpose_f64(m, m, Rt, m, L, ldl, stream);                                       // L = R'^T
+  PURL_TRY(transpose_f64(m, m, Rt, m, L, ldl, stream));                                   // L = R'^T
+  PURL_TRY(finite_poison(w.finite, m, m, U, ldu, stream));
+  PURL_TRY(finite_poison(w.finite, m, m, L, ldl, stream));
+  return finite_poison(w.finite, n, m, V, ldv, stream);
 }
 
 int purl_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double *G, int ldg,
@@ -431,8 +441,10 @@ int purl_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double 
 size_t purl_qr_workspace_bytes(int m, int n, int mode) {
   if (m < 0 || n < 0 || m < n || !mode_ok(mode) || !emu_rows_ok(mode, m)) return 0;
   Arena ar;
+  int *flag = ar.take<int>(1);
   double *F = ar.take<double>((size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1));
   (void)F;
+  (void)flag;
   if (mode == PURL_MODE_FP64) {
     QrWork w;
     if (qr_plan(ar, m, n, mode, &w) != PURL_OK) return 0;
@@ -462,21 +474,27 @@ int purl_qr(int m, int n, const double *M, int ldm, double *Q, int ldq, double *
   Arena ar;
   ar.base = static_cast<char *>(scratch.ptr);
   ar.size = workspace ? workspace_bytes : need;
+  int *flag = ar.take<int>(1);
   double *F = ar.take<double>((size_t)m * n);
   if (mode == PURL_MODE_FP64) {
     QrWork w;
     PURL_TRY(qr_plan(ar, m, n, mode, &w));
     if (!ar.ok) return PURL_ERR_NOMEM;
+    PURL_TRY(finite_check(m, n, M, ldm, flag, stream));
     PURL_TRY(copy_matrix(m, n, M, ldm, F, m, stream));
-    return qr_explicit(m, n, F, m, Q, ldq, R, ldr, mode, w, stream);
+    PURL_TRY(qr_explicit(m, n, F, m, Q, ldq, R, ldr, mode, w, stream));
+  } else {
+    QrMixWork w;
+    PURL_TRY(qr_mixed_plan(ar, m, n, mode == PURL_MODE_FP64_EMU ? kTcxEmuSlices : kFinalSlices, &w));
+    if (!ar.ok) return PURL_ERR_NOMEM;
+    PURL_TRY(finite_check(m, n, M, ldm, flag, stream));
+    PURL_TRY(copy_matrix(m, n, M, ldm, F, m, stream));
+    PURL_TRY(qr_mixed_factor(m, n, F, m, w, stream));
+    if (Q) PURL_TRY(qr_mixed_form_q(m, n, F, m, w, Q, ldq, stream));
+    PURL_TRY(qr_sign_fix(m, n, F, m, Q, ldq, R, ldr, stream));
   }
-  QrMixWork w;
-  PURL_TRY(qr_mixed_plan(ar, m, n, mode == PURL_MODE_FP64_EMU ? kTcxEmuSlices : kFinalSlices, &w));
-  if (!ar.ok) return PURL_ERR_NOMEM;
-  PURL_TRY(copy_matrix(m, n, M, ldm, F, m, stream));
-  PURL_TRY(qr_mixed_factor(m, n, F, m, w, stream));
-  if (Q) PURL_TRY(qr_mixed_form_q(m, n, F, m, w, Q, ldq, stream));
-  return qr_sign_fix(m, n, F, m, Q, ldq, R, ldr, stream);
+  PURL_TRY(finite_poison(flag, m, n, Q, ldq, stream));
+  return finite_poison(flag, n, n, R, ldr, stream);
 }
 
 int purl_gemm_f64(char transa, char transb, int m, int n, int k, double alpha, const double *A,
@@ -601,7 +619,10 @@ int purl_device_status(cudaStream_t stream) {
   if (cudaMemcpy(&h, di->ctrl, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return PURL_ERR_CUDA;
   DeviceControl z{};
   if (cudaMemcpy(di->ctrl, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return PURL_ERR_CUDA;
-  return h.status;
+  // the allocation-free entry point reports to a word of its own static array
+  int na = PURL_OK;
+  if (noalloc_take_status(&na) != PURL_OK) return PURL_ERR_CUDA;
+  return h.status != PURL_OK ? h.status : na;
 }
 
 }  // extern "C"

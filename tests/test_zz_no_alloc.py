@@ -61,6 +61,23 @@ def test_noalloc_matches_allocating_entry_on_consecutive_calls(B, S, ta, tb, m, 
     assert B.purl_device_status() == B.PURL_OK
 
 
+def test_noalloc_timeout_reaches_device_status(B):
+    # A bounded wait that runs out while reporting to the no-alloc array's own
+    # status word (a grid barrier that awaits one block too many, short poll
+    # limit) must come back through purl_device_status and then be cleared.
+    assert B.purl_device_status() == B.PURL_OK
+    B.purl_wait_probe_noalloc(4, True, 1 << 14)
+    assert B.purl_device_status() == B.PURL_ERR_TIMEOUT
+    assert B.purl_device_status() == B.PURL_OK
+    # the entry point still gives the allocating entry point's result afterwards
+    rng = np.random.default_rng(5)
+    A, Bm = rng.standard_normal((96, 80)), rng.standard_normal((80, 40))
+    got = _host(B.purl_gemm_tc_noalloc("N", "N", _dev(A), _dev(Bm), slices=2))
+    ref = _host(B.purl_gemm_tc("N", "N", _dev(A), _dev(Bm), slices=2))
+    assert np.all(np.abs(got - ref) <= _bound(2, 80) * np.abs(A) @ np.abs(Bm))
+    assert B.purl_device_status() == B.PURL_OK
+
+
 def test_noalloc_rejects_requests_beyond_its_scratch(B):
     import torch
     L = B.lib()
