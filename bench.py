@@ -83,11 +83,18 @@ def parse():
     ap.add_argument("--rank", type=int, default=256, help="rsvd: target rank l")
     ap.add_argument("--count", type=int, default=4096, help="batched: number of matrices")
     ap.add_argument("--variant", type=int, default=-1, help="batched: kernel variant (-1 = autotune)")
-    ap.add_argument("--fp64-n", type=int, default=8192,
-                    help="size of the FP64-path comparison run (0 = skip); FP64 at n=16384 takes minutes")
+    ap.add_argument("--fp64-n", type=int, default=-1,
+                    help="size of the native FP64 comparison run (-1 = the bench's n, 0 = skip; "
+                         "about 94 s at n=16384)")
+    ap.add_argument("--fp64emu-n", type=int, default=-1,
+                    help="mixed mode: size of the FP64-emulation comparison run (-1 = the bench's n, 0 = skip)")
     a = ap.parse_args()
     a.m = a.m or a.n
     a.reorth = not a.no_reorth
+    if a.fp64_n < 0:
+        a.fp64_n = a.n
+    if a.fp64emu_n < 0:
+        a.fp64emu_n = a.n
     return a
 
 
@@ -292,27 +299,37 @@ def run_ours(a):
         e2e = end_to_end(a, A, U, R, V, ws, mode, seed, world, dev, B)
 
     # ---- the FP64 path on the same recipe (the "vs FP64" of the metric) ----
-    fp64 = None
-    if a.mode in ("mixed", "fp64emu") and a.fp64_n > 0:
+    fp64 = fp64emu = None
+    if a.mode in ("mixed", "fp64emu") and (a.fp64_n > 0 or a.fp64emu_n > 0):
         del ws
         torch.cuda.empty_cache()
-        fp64 = fp64_compare(a, dev, B, W, seed)
+    if a.mode in ("mixed", "fp64emu") and a.fp64_n > 0:
+        fp64 = fp64_compare(a, dev, B, W, seed, B.PURL_MODE_FP64, a.fp64_n, A)
+    if a.mode == "mixed" and a.fp64emu_n > 0:
+        fp64emu = fp64_compare(a, dev, B, W, seed, B.PURL_MODE_FP64_EMU, a.fp64emu_n, A)
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel class ----
-    roof = roofline(prof, prof_named, a.steps, a.mode)
+    # ---- roofline of the dominant kernel function ----
+    clocks = clk.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = roofline(prof, prof_named, a.steps, a.mode, sm_mhz=clocks.get("sm_mhz"), sms=sms)
     if roof is not None and prof_named:
-        roof["share_of_step"] = prof_named[roof["kernel"]]["ms"] / a.steps / ms_step
+        roof["share_of_step"] = by_function(prof_named)[roof["kernel"]]["ms"] / a.steps / ms_step
+        attach_traffic(roof)
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         v, t, cores = cpu_oracle_run(a.cpu_sample_n, q, reorth)
         cpu = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                "sample": f"PowerURV m=n={a.cpu_sample_n} q={q} reorth={int(reorth)}, FP64 C oracle "
                          f"(OpenMP), one factorization, {t:.2f} s"}
+    # The stdout line stays short (the accuracy gate of the metric and the FP64 comparison come
+    # before anything long); the per-kernel breakdown goes to stderr as a second JSON object.
+    acc = {"recon_rel_fro": errs["recon_rel_fro"], "orth_U_fro": errs["orth_U_fro"],
+           "orth_V_fro": errs["orth_V_fro"], "meets_1e-6": errs["recon_rel_fro"] <= 1e-6}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -324,49 +341,67 @@ def run_ours(a):
                               else "Haar factors, sigma 10^(-6(j-1)/(n-1))"), "parallelism": f"replicas{world}",
                    "l2": f"inputs larger than L2 (A is {8 * m * n / 2**30:.1f} GiB)"},
         "sec_per_factorization": ms_step * 1e-3,
+        "accuracy": acc,
         "fp64_path": fp64,
-        "speedup_vs_fp64_path": (value / fp64["tflops"]) if fp64 else None,
+        "speedup_vs_fp64_path": ((fp64["sec"] / (ms_step * 1e-3)) if (fp64["m"], fp64["n"]) == (m, n)
+                                 else value / fp64["tflops"]) if fp64 else None,
+        "fp64emu_path": fp64emu,
         "flops_per_step": flops,
-        "errors": errs,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": int(launches),
-        "clocks": clk.summary(),
-        "kernels": prof,
-        "kernels_by_name": ({k: {"launches": v["launches"], "ms_per_step": v["ms"] / a.steps,
-                                 "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9}
-                             for k, v in sorted(prof_named.items(), key=lambda kv: -kv[1]["ms"])}
-                            if prof_named else None),
     }
     print(json.dumps(line), flush=True)
+    if prof_named:
+        funcs = by_function(prof_named)
+        detail = {"kernel_classes": prof,
+                  "kernel_functions_ms_per_step": {k: round(v["ms"] / a.steps, 3) for k, v in
+                                                   sorted(funcs.items(), key=lambda kv: -kv[1]["ms"])},
+                  "labels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / a.steps,
+                                 "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9}
+                             for k, v in sorted(prof_named.items(), key=lambda kv: -kv[1]["ms"])}}
+        print("per-kernel " + json.dumps(detail), file=sys.stderr, flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
-def fp64_compare(a, dev, B, W, seed):
-    """Time the FP64 path (1 warm-up, 1 timed) at n = a.fp64_n on the same recipe."""
+def fp64_compare(a, dev, B, W, seed, mode, n, A_main=None):
+    """Time an FP64-accurate mode (native FP64, or FP64 emulated on the tensor cores) at size n on the
+    same recipe: one factorization at n = 1024 first (kernel attributes, allocator), then one timed
+    factorization at n with CUDA events, and its probe errors."""
     import torch
-    n = a.fp64_n
     m = n if a.m == a.n else int(round(a.m * n / a.n))
-    A = W.test_matrix_torch(m, n, W.sigma_profile("exponential", n, decades=6), device=dev)
-    U, R, V = B.empty_colmajor(m, n, dev), B.empty_colmajor(n, n, dev), B.empty_colmajor(n, n, dev)
-    ws = torch.empty(B.purl_urv_workspace_bytes(m, n, B.PURL_MODE_FP64), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    B.purl_urv_factor(A, a.q, a.reorth, seed, mode=B.PURL_MODE_FP64, out=(U, R, V), workspace=ws, stream=stream)
+    w = min(n, 1024)
+    Aw = W.gaussian_matrix_torch(w, w, 99, device=dev)
+    B.purl_urv_factor(Aw, a.q, a.reorth, seed, mode=mode, stream=stream)
+    torch.cuda.synchronize()
+    del Aw
+    if A_main is not None and tuple(A_main.shape) == (m, n) and a.matrix == "haar":
+        A = A_main  # the same matrix the timed steps factored
+    else:
+        A = W.test_matrix_torch(m, n, W.sigma_profile("exponential", n, decades=6), device=dev)
+    U, R, V = B.empty_colmajor(m, n, dev), B.empty_colmajor(n, n, dev), B.empty_colmajor(n, n, dev)
+    ws = torch.empty(B.purl_urv_workspace_bytes(m, n, mode), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    B.purl_urv_factor(A, a.q, a.reorth, seed, mode=B.PURL_MODE_FP64, out=(U, R, V), workspace=ws, stream=stream)
+    B.purl_urv_factor(A, a.q, a.reorth, seed, mode=mode, out=(U, R, V), workspace=ws, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    if B.purl_device_status() != B.PURL_OK:
+        raise RuntimeError("device status not ok after the FP64 comparison run")
     sec = e0.elapsed_time(e1) * 1e-3
     errs = probe_errors(A, U, R, V)
+    del ws, A, U, R, V
+    torch.cuda.empty_cache()
     return {"m": m, "n": n, "q": a.q, "reorth": a.reorth, "sec": sec,
-            "tflops": urv_flops(m, n, a.q, a.reorth) / sec / 1e12, "errors": errs,
-            "note": "FP64 path timed at this size (1 warm-up + 1 timed factorization); its TFLOP/s is the "
-                    "FP64-pipe rate, which does not grow with n beyond this size"}
+            "tflops": urv_flops(m, n, a.q, a.reorth) / sec / 1e12,
+            "recon_rel_fro": errs["recon_rel_fro"], "orth_U_fro": errs["orth_U_fro"],
+            "orth_V_fro": errs["orth_V_fro"], "timed": "1 factorization (after one at n=1024)"}
 
 
 def probe_errors(A, U, R, V, k: int = 16):
@@ -478,30 +513,85 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# FP64 DFMA peak of this GPU, measured with a DFMA-loop kernel (2 DFMA/clk/SM
-# x 152 SMs at the clock under load); MEASURED_PEAKS.json carries no FP64 figure.
-FP64_DFMA_PEAK_TFLOPS = 1.20
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel function, averaged
+# over every launch of one ncu capture of the bench's own step (summary and command under profiles/).
+# It is reported only while the kernel's source file still has the hash it had when captured.
+TRAFFIC = {}
 
 
-def roofline(prof, named, steps, mode):
-    """Roofline of the dominant kernel (by device time in the timed region).
+def _sha16(path: str) -> str:
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
-    Tensor-core kernels: issued BF16 flops (2 m n k per slice pair) over their
-    event-timed duration against the measured sustained BF16 peak; FP64 DFMA
-    kernels: FP64 flops against the measured DFMA peak; everything else:
-    algorithmic bytes against the measured copy bandwidth."""
-    if not named:
+
+def attach_traffic(roof):
+    t = TRAFFIC.get(roof.get("kernel"))
+    if not t:
+        return
+    try:
+        same = _sha16(os.path.join(ROOT, t["src"])) == t["sha16"]
+    except OSError:
+        same = False
+    if same:
+        roof["traffic"] = t["bytes_per_launch"]
+        roof["traffic_source"] = t["profile"]
+    else:
+        roof["traffic_note"] = f"{t['src']} changed since the ncu capture ({t['profile']})"
+
+
+def fp64_peak_tflops(sm_mhz: float | None, sms: int = 152) -> float:
+    """FP64 DFMA peak from the unit count and the SM clock sampled under load: 2 DFMA per clock per SM
+    (4 flops), i.e. 1.26 TFLOP/s for 152 SMs at the 2070 MHz maximum (nominal GB300 FP64: 1.25)."""
+    return sms * 4.0 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
+def kernel_function(label: str) -> str:
+    """The CUDA kernel function a profiler label belongs to.  The tensor-core engines book their
+    launches under call-site tags ("tcx outer update", "tcx emu A Y", "tc noalloc", ...), which
+    name their kernel by prefix; every other label is the kernel's own name."""
+    if label.startswith("tcx"):
+        return "tcx_gemm_kernel"
+    if label == "tc_gemm_kernel" or label.startswith("tc "):
+        return "tc_gemm_kernel"
+    return label
+
+
+def by_function(named):
+    """Per-label totals summed per kernel function; each function keeps its call sites."""
+    out = {}
+    for label, st in (named or {}).items():
+        agg = out.setdefault(kernel_function(label),
+                             {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0, "sites": {}})
+        for k in ("launches", "ms", "flops", "bytes"):
+            agg[k] += st[k]
+        agg["sites"][label] = st
+    return out
+
+
+def roofline(prof, named, steps, mode, sm_mhz=None, sms=152):
+    """Roofline of the dominant kernel function (by device time in the timed region).
+
+    Call-site labels are summed per kernel function first.  Tensor-core kernels: issued BF16 flops
+    (2 m n k per slice pair) over their event-timed duration against the measured sustained BF16
+    peak; FP64 DFMA kernels: FP64 flops against the DFMA peak at the sampled SM clock; everything
+    else: algorithmic bytes against the measured copy bandwidth."""
+    funcs = by_function(named)
+    if not funcs:
         return None
     peaks, src = _peaks()
-    name = max(named, key=lambda k: named[k]["ms"])
-    st = named[name]
+    name = max(funcs, key=lambda k: funcs[k]["ms"])
+    st = funcs[name]
     if st["launches"] == 0 or st["ms"] <= 0:
         return None
     sec = st["ms"] * 1e-3
     base = {"kernel": name, "launches_per_step": st["launches"] / steps,
             "avg_launch_ms": st["ms"] / st["launches"], "traffic": None,
             "share_of_step": None, "hbm_gbs_algorithmic": st["bytes"] / sec / 1e9}
-    if name.startswith("tc") or name == "tc_gemm_kernel":
+    if len(st["sites"]) > 1:
+        base["call_sites_ms_per_step"] = {k: round(v["ms"] / steps, 2) for k, v in
+                                          sorted(st["sites"].items(), key=lambda kv: -kv[1]["ms"])[:8]}
+    if name in ("tcx_gemm_kernel", "tc_gemm_kernel"):
         achieved = st["flops"] / sec / 1e12
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         base.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -510,16 +600,17 @@ def roofline(prof, named, steps, mode):
         return base
     if name in ("panel_kernel", "gemm_f64_kernel", "gram_kernel") or name.startswith("gemm_f64"):
         achieved = st["flops"] / sec / 1e12
-        base.update({"bound": "alu", "achieved": achieved, "peak": FP64_DFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_DFMA_PEAK_TFLOPS,
-                     "peak_source": "measured FP64 DFMA loop, 2 DFMA/clk/SM x 152 SMs"})
+        peak = fp64_peak_tflops(sm_mhz, sms)
+        base.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak,
+                     "peak_source": f"FP64 DFMA: {sms} SMs x 2 DFMA/clk x 2 flops x "
+                                    f"{(sm_mhz or 2070.0):.0f} MHz (sampled SM clock)"})
         return base
     achieved = st["bytes"] / sec / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
     base.update({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                  "peak_source": f"{src} hbm copy"})
     return base
-
 
 
 # ------------------------------------------------------------- batched -----
@@ -819,7 +910,9 @@ def run_adjoint(a):
     B.purl_profile_enable(False)
     sec = e0.elapsed_time(e1) / a.steps * 1e-3
     F = adjoint_flops(m, n, q, reorth)
-    roof = roofline(None, named, a.steps, "fp64")
+    clocks = clk.summary()
+    roof = roofline(None, named, a.steps, "fp64", sm_mhz=clocks.get("sm_mhz"),
+                    sms=torch.cuda.get_device_properties(dev).multi_processor_count)
     # end to end: A and cotangents from pinned host memory, gradient back
     hA, hU = A.cpu().pin_memory(), Ub.cpu().pin_memory()
     hR, hV, hAb = Rb.cpu().pin_memory(), Vb.cpu().pin_memory(), torch.empty_like(Ab.cpu()).pin_memory()
@@ -847,7 +940,7 @@ def run_adjoint(a):
         "tflops": F / sec / 1e12, "flops_per_step": F, "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_sec, "unit": "s", "h2d_bytes_per_step": 8 * (2 * m * n + 2 * n * n),
                 "d2h_bytes_per_step": 8 * m * n},
-        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "gpu_launches": int(launches), "clocks": clocks,
         "kernels_by_name": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / a.steps}
                             for k, v in sorted(named.items(), key=lambda kv: -kv[1]["ms"])[:8]},
     }
@@ -942,7 +1035,9 @@ def run_rsvd(a):
     B.purl_profile_enable(False)
     sec = e0.elapsed_time(e1) / a.steps * 1e-3
     F = rsvd_flops(m, n, l, q, reorth)
-    roof = roofline(None, named, a.steps, "fp64")
+    clocks = clk.summary()
+    roof = roofline(None, named, a.steps, "fp64", sm_mhz=clocks.get("sm_mhz"),
+                    sms=torch.cuda.get_device_properties(dev).multi_processor_count)
     # accuracy against the exact spectrum of the synthetic matrix (sigma_j prescribed)
     sig = torch.as_tensor(W.sigma_profile("exponential", n, decades=6)[:l], device=dev)
     sv_err = float(((S - sig).abs() / sig[0]).max())
@@ -971,7 +1066,7 @@ def run_rsvd(a):
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_sec, "unit": "s", "h2d_bytes_per_step": 8 * m * n,
                 "d2h_bytes_per_step": 8 * (m * l + l + n * l)},
-        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "gpu_launches": int(launches), "clocks": clocks,
         "kernels_by_name": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / a.steps}
                             for k, v in sorted(named.items(), key=lambda kv: -kv[1]["ms"])[:8]},
     }

@@ -452,7 +452,7 @@ extern "C" int purl_gemm_tc_noalloc(char transa, char transb, int m, int n, int 
   if (k == 0) {
     long long g = ((long long)m * n + 255) / 256;
     if (g > (long long)sms * 16) g = (long long)sms * 16;
-    LaunchScope ls(KC_OTHER, stream, 0.0, 16.0 * m * n, "tc noalloc scale");
+    LaunchScope ls(KC_OTHER, stream, 0.0, 16.0 * m * n, "noalloc_scale_kernel");
     noalloc_scale_kernel<<<(int)g, 256, 0, stream>>>(m, n, beta, C, ldc);
     return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
   }
@@ -464,12 +464,12 @@ extern "C" int purl_gemm_tc_noalloc(char transa, char transb, int m, int n, int 
     if (transposed) {
       dim3 grid(ceil_div(R, 32), ceil_div(Cc, 32));
       if (grid.y > 65535) return PURL_ERR_UNSUPPORTED;
-      LaunchScope ls(KC_SPLIT, stream, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc, "tc noalloc split");
+      LaunchScope ls(KC_SPLIT, stream, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc, "split_t_kernel");
       split_t_kernel<<<grid, dim3(32, 8), 0, stream>>>(R, Cc, X, ldx, dst);
     } else {
       long long g = ((long long)R * Cc + 255) / 256;
       if (g > (long long)sms * 16) g = (long long)sms * 16;
-      LaunchScope ls(KC_SPLIT, stream, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc, "tc noalloc split");
+      LaunchScope ls(KC_SPLIT, stream, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc, "split_kernel");
       split_kernel<<<(int)g, 256, 0, stream>>>(R, Cc, X, ldx, dst);
     }
     return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;

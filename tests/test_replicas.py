@@ -74,17 +74,40 @@ def test_roofline_picks_the_dominant_kernel_and_its_peak():
         "split_exact_kernel": {"launches": 50, "ms": 100.0, "flops": 0.0, "bytes": 3e11},
     }
     r = bench.roofline(None, named, steps, "mixed")
-    assert r["kernel"] == "tcx outer update" and r["bound"] == "tensor"
+    assert r["kernel"] == "tcx_gemm_kernel" and r["bound"] == "tensor"
     assert r["achieved"] == pytest.approx(2.0e14 / 0.5 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / peaks.get("bf16_tflops_sustained", 1700.0))
     assert r["launches_per_step"] == 5 and r["avg_launch_ms"] == pytest.approx(50.0)
-    # FP64 kernels against the DFMA peak, everything else against the copy bandwidth
+    # FP64 kernels against the DFMA peak at the sampled clock, everything else against the copy bandwidth
     named["tcx outer update"]["ms"] = 1.0
-    r = bench.roofline(None, named, steps, "mixed")
+    r = bench.roofline(None, named, steps, "mixed", sm_mhz=1900.0, sms=152)
     assert r["kernel"] == "panel_kernel" and r["bound"] == "alu"
-    assert r["frac"] == pytest.approx(2.0e10 / 0.3 / 1e12 / bench.FP64_DFMA_PEAK_TFLOPS)
+    assert r["peak"] == pytest.approx(152 * 4 * 1900e6 / 1e12)
+    assert r["frac"] == pytest.approx(2.0e10 / 0.3 / 1e12 / r["peak"])
     named["panel_kernel"]["ms"] = 1.0
     r = bench.roofline(None, named, steps, "mixed")
     assert r["kernel"] == "split_exact_kernel" and r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(3e11 / 0.1 / 1e9)
     assert bench.roofline(None, {}, steps, "mixed") is None
+
+
+def test_roofline_sums_call_sites_per_kernel_function():
+    # no single call site of the exact engine beats the panel, but together they do
+    import bench
+    named = {
+        "tcx outer update": {"launches": 10, "ms": 250.0, "flops": 1.0e14, "bytes": 1e12},
+        "tcx outer C^T V~": {"launches": 10, "ms": 200.0, "flops": 0.8e14, "bytes": 1e12},
+        "tcx inner update": {"launches": 100, "ms": 100.0, "flops": 0.1e14, "bytes": 1e11},
+        "panel_kernel": {"launches": 100, "ms": 300.0, "flops": 2.0e10, "bytes": 1e9},
+        "tc_gemm_kernel": {"launches": 4, "ms": 20.0, "flops": 2.0e13, "bytes": 1e10},
+        "tc noalloc": {"launches": 1, "ms": 1.0, "flops": 1.0e12, "bytes": 1e9},
+    }
+    r = bench.roofline(None, named, 1, "mixed")
+    assert r["kernel"] == "tcx_gemm_kernel"
+    assert r["launches_per_step"] == 120
+    assert r["achieved"] == pytest.approx(1.9e14 / 0.55 / 1e12)
+    assert list(r["call_sites_ms_per_step"]) == ["tcx outer update", "tcx outer C^T V~", "tcx inner update"]
+    funcs = bench.by_function(named)
+    assert funcs["tc_gemm_kernel"]["launches"] == 5
+    assert bench.kernel_function("tcx emu A Y") == "tcx_gemm_kernel"
+    assert bench.kernel_function("split_exact_kernel") == "split_exact_kernel"
