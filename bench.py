@@ -67,7 +67,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["mixed", "fp64", "fp64emu"], default="mixed")
+    ap.add_argument("--mode", choices=["mixed", "mixed16", "fp64", "fp64emu"], default="mixed",
+                    help="mixed: BF16 power steps; mixed16: FP16 power steps; fp64; fp64emu")
     ap.add_argument("--m", type=int, default=0, help="rows (default n)")
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--q", type=int, default=2)
@@ -236,7 +237,8 @@ def run_ours(a):
     dev = torch.device("cuda", torch.cuda.current_device())
     Bld.build()
     B.lib()
-    mode = {"mixed": B.PURL_MODE_MIXED_BF16, "fp64": B.PURL_MODE_FP64, "fp64emu": B.PURL_MODE_FP64_EMU}[a.mode]
+    mode = {"mixed": B.PURL_MODE_MIXED_BF16, "mixed16": B.PURL_MODE_MIXED_FP16, "fp64": B.PURL_MODE_FP64,
+            "fp64emu": B.PURL_MODE_FP64_EMU}[a.mode]
     m, n, q, reorth = a.m, a.n, a.q, a.reorth
 
     if a.matrix == "gaussian":
@@ -300,12 +302,12 @@ def run_ours(a):
 
     # ---- the FP64 path on the same recipe (the "vs FP64" of the metric) ----
     fp64 = fp64emu = None
-    if a.mode in ("mixed", "fp64emu") and (a.fp64_n > 0 or a.fp64emu_n > 0):
+    if a.mode in ("mixed", "mixed16", "fp64emu") and (a.fp64_n > 0 or a.fp64emu_n > 0):
         del ws
         torch.cuda.empty_cache()
-    if a.mode in ("mixed", "fp64emu") and a.fp64_n > 0:
+    if a.mode in ("mixed", "mixed16", "fp64emu") and a.fp64_n > 0:
         fp64 = fp64_compare(a, dev, B, W, seed, B.PURL_MODE_FP64, a.fp64_n, A)
-    if a.mode == "mixed" and a.fp64emu_n > 0:
+    if a.mode in ("mixed", "mixed16") and a.fp64emu_n > 0:
         fp64emu = fp64_compare(a, dev, B, W, seed, B.PURL_MODE_FP64_EMU, a.fp64emu_n, A)
 
     if rank != 0:
@@ -334,7 +336,8 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "data": "synthetic",
-        "dtype": {"mixed": "bf16+f64", "fp64": "f64", "fp64emu": "f64 (emulated: 8 bf16 slices, exact sums)"}[a.mode],
+        "dtype": {"mixed": "bf16+f64", "mixed16": "fp16+bf16+f64", "fp64": "f64",
+                  "fp64emu": "f64 (emulated: 8 bf16 slices, exact sums)"}[a.mode],
         "config": {"workload": f"PowerURV m={m} n={n} q={q} reorth={int(reorth)} {a.mode}",
                    "m": m, "n": n, "q": q, "reorth": reorth, "mode": a.mode,
                    "matrix": ("Gaussian entries" if a.matrix == "gaussian"

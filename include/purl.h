@@ -59,11 +59,20 @@ extern "C" {
 /* precision modes for purl_urv_factor_ex / purl_qr */
 #define PURL_MODE_FP64 0
 /* Power-step products A Y and A^T Z on BF16 tensor cores with FP32
- * accumulation (one BF16 slice per operand); A V, every QR trailing update,
+ * accumulation (one plain BF16 slice per operand, scaled as described under
+ * PURL_MODE_MIXED_FP16); A V, every QR trailing update,
  * T factor and Q formation as exact-accumulation products of fixed-point BF16
  * slices (2 slices in the power iteration's re-orthonormalisations, 4 in the
  * QRs of Eqs. (5)-(6) and in A V); Householder panels in FP64. */
 #define PURL_MODE_MIXED_BF16 2
+/* As PURL_MODE_MIXED_BF16 with the power-step products A Y and A^T Z on FP16
+ * operands (11-bit significands instead of BF16's 8, FP32 accumulation).  In
+ * both mixed modes every power-step operand is sliced as 2^s X, the power of
+ * two chosen on the device from X's largest entry (FP16 holds magnitudes up
+ * to 65504 only); the scale is never undone because each product is
+ * orthonormalised next, or only its span enters the QR of Eq. (5).  purl_qr
+ * treats this mode as PURL_MODE_MIXED_BF16 (a QR has no power steps). */
+#define PURL_MODE_MIXED_FP16 3
 /* FP64 emulated on the BF16 tensor cores: the FP64 mode's algorithm with
  * every product (A Y, A^T Z, A V, every QR trailing update, Gram matrix and
  * Q formation) an exact-accumulation product of 8 fixed-point BF16 slices per

@@ -25,6 +25,7 @@ PURL_ERR_NOMEM = 4
 PURL_ERR_UNSUPPORTED = 5
 PURL_MODE_FP64 = 0
 PURL_MODE_MIXED_BF16 = 2
+PURL_MODE_MIXED_FP16 = 3
 PURL_MODE_FP64_EMU = 4
 
 # (name, restype, argtypes) for every symbol include/purl.h declares

@@ -15,6 +15,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <mutex>
 
@@ -48,7 +49,7 @@ template <int BN, int S>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    TcView va, TcView vb, int M, int N, int K, int k_chunk, TcEpilogue ep,
-                   DeviceControl *ctrl) {
+                   DeviceControl *ctrl, uint32_t idesc) {
   using Cfg = TcCfg<BN, S>;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
@@ -119,7 +120,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
       for (int kb = 0; kb < nkb; ++kb) {
         const int st = kb % STAGES;
         const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
@@ -222,9 +222,74 @@ __global__ void split_t_kernel(int R, int Cc, const double *__restrict__ X, long
   }
 }
 
+// ------------------------------------------------- scaled plain slices ----
+// Largest biased exponent field of the entries of X (atomicMax into *e).
+__global__ void max_exp_kernel(int R, int Cc, const double *__restrict__ X, long long ldx, int *e) {
+  long long total = (long long)R * Cc;
+  int mx = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i % R), c = (int)(i / R);
+    const int ex = (int)((__double_as_longlong(X[r + c * ldx]) >> 52) & 0x7ff);
+    mx = ex > mx ? ex : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(e, mx);
+}
+
+// Power of two 2^s that puts the largest entry (below 2^(e - 1022)) just
+// under 2^15 for FP16 or 2 for BF16; clamped so that the factor 2^s is a normal
+// number (the scaling is exact unless an entry leaves the FP64 range).
+__device__ __forceinline__ int slice_shift(int e, bool f16) {
+  const int top = (f16 ? 15 : 1) - (e - 1022);
+  return top < -1000 ? -1000 : (top > 1000 ? 1000 : top);
+}
+
+// 2^sh as a double (|sh| <= 1000: a normal number), built from its bits
+__device__ __forceinline__ double pow2(int sh) { return __longlong_as_double((long long)(1023 + sh) << 52); }
+
+__device__ __forceinline__ __nv_bfloat16 to_plain16(double x, bool f16) {
+  if (f16) {
+    const __half h = __double2half(x);
+    return *reinterpret_cast<const __nv_bfloat16 *>(&h);
+  }
+  return __double2bfloat16(x);
+}
+
+__global__ void split_scaled_kernel(int R, int Cc, const double *__restrict__ X, long long ldx, Slices dst,
+                                    const int *e) {
+  const bool f16 = dst.f16 != 0;
+  const double sc = pow2(slice_shift(*e, f16));
+  long long total = (long long)R * Cc;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i % R), c = (int)(i / R);
+    dst.base[r + c * dst.ld] = to_plain16(X[r + c * ldx] * sc, f16);
+  }
+}
+
+// dst (Cc x R) = 2^s X^T; 32 x 32 tiles through shared memory.
+__global__ void split_scaled_t_kernel(int R, int Cc, const double *__restrict__ X, long long ldx, Slices dst,
+                                      const int *e) {
+  __shared__ double tile[32][33];
+  const bool f16 = dst.f16 != 0;
+  const double sc = pow2(slice_shift(*e, f16));
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    int r = r0 + threadIdx.x, c = c0 + j;
+    tile[j][threadIdx.x] = (r < R && c < Cc) ? X[r + (long long)c * ldx] : 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    int c = c0 + threadIdx.x, r = r0 + j;
+    if (r < R && c < Cc) dst.base[c + (long long)r * dst.ld] = to_plain16(tile[threadIdx.x][j] * sc, f16);
+  }
+}
+
 template <int BN, int S>
 int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcView va, TcView vb, int M, int N, int K,
-              int k_chunk, int splits, const TcEpilogue &ep, DeviceControl *ctrl, cudaStream_t s) {
+              int k_chunk, int splits, const TcEpilogue &ep, DeviceControl *ctrl, uint32_t idesc, cudaStream_t s) {
   using Cfg = TcCfg<BN, S>;
   static thread_local int attr_dev = -1;
   int dev = 0;
@@ -245,7 +310,7 @@ int launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, TcView va, TcView vb
                                : 4.0 * M * N * splits);
   (void)prods;
   LaunchScope ls(KC_GEMM_TC, s, flops, bytes, ep.tag ? ep.tag : "tc_gemm_kernel");
-  tc_gemm_kernel<BN, S><<<grid, TC_THREADS, Cfg::SMEM, s>>>(ma, mb, va, vb, M, N, K, k_chunk, ep, ctrl);
+  tc_gemm_kernel<BN, S><<<grid, TC_THREADS, Cfg::SMEM, s>>>(ma, mb, va, vb, M, N, K, k_chunk, ep, ctrl, idesc);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
@@ -276,7 +341,8 @@ int make_map(CUtensorMap *map, const Slices &X, int k_end, int c_end, int box_ro
   cuuint64_t strides[2] = {(cuuint64_t)X.ld * 2, (cuuint64_t)X.plane * 2};
   cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, X.base, dims, strides, box, estr,
+  CUresult r = enc(map, X.f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, X.base, dims,
+                   strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? PURL_OK : PURL_ERR_UNSUPPORTED;
@@ -304,6 +370,35 @@ int split_slices_t(int R, int Cc, const double *X, long long ldx, Slices dst, cu
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
+int split_scaled(int R, int Cc, const double *X, long long ldx, Slices dst, int *e_ws, bool transposed,
+                 cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  const long long total = (long long)R * Cc;
+  if (total == 0) return PURL_OK;
+  if (dst.S != 1) return PURL_ERR_UNSUPPORTED;
+  PURL_CUDA_TRY(cudaMemsetAsync(e_ws, 0, sizeof(int), s));
+  long long g = (total + 255) / 256;
+  if (g > (long long)di->num_sms * 8) g = (long long)di->num_sms * 8;
+  {
+    LaunchScope ls(KC_SPLIT, s, 0.0, 8.0 * total, "max_exp_kernel");
+    max_exp_kernel<<<(int)g, 256, 0, s>>>(R, Cc, X, ldx, e_ws);
+  }
+  PURL_CUDA_TRY(cudaGetLastError());
+  if (transposed) {
+    dim3 grid(ceil_div(R, 32), ceil_div(Cc, 32));
+    if (grid.y > 65535) return PURL_ERR_UNSUPPORTED;
+    LaunchScope ls(KC_SPLIT, s, 0.0, 10.0 * total, "split_scaled_t_kernel");
+    split_scaled_t_kernel<<<grid, dim3(32, 8), 0, s>>>(R, Cc, X, ldx, dst, e_ws);
+  } else {
+    long long g2 = (total + 255) / 256;
+    if (g2 > (long long)di->num_sms * 16) g2 = (long long)di->num_sms * 16;
+    LaunchScope ls(KC_SPLIT, s, 0.0, 10.0 * total, "split_scaled_kernel");
+    split_scaled_kernel<<<(int)g2, 256, 0, s>>>(R, Cc, X, ldx, dst, e_ws);
+  }
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
+
 void tc_choose_splits(int M, int N, int K, int num_sms, int max_splits, int *splits, int *k_chunk) {
   long long tiles = (long long)ceil_div(M, TC_BM) * ceil_div(N, 128);
   long long want = (2LL * num_sms + tiles - 1) / tiles;
@@ -324,6 +419,8 @@ int tc_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0,
   if (M <= 0 || N <= 0) return PURL_OK;
   if (K <= 0 || k_chunk <= 0 || (k_chunk % TC_BK) != 0 || splits != ceil_div(K, k_chunk)) return PURL_ERR_UNSUPPORTED;
   if (S < 1 || S > 3 || A.S < S || B.S < S) return PURL_ERR_UNSUPPORTED;
+  // one operand type per MMA: never mix FP16 and BF16 (FP16 only as one plain slice)
+  if (A.f16 != B.f16 || (A.f16 && S != 1)) return PURL_ERR_UNSUPPORTED;
   if ((a_r0 % 8) != 0 || (b_r0 % 8) != 0) return PURL_ERR_UNSUPPORTED;
   if (ep.mode == 1 && !ep.P) return PURL_ERR_UNSUPPORTED;
   if (ep.mode == 0 && !ep.C) return PURL_ERR_UNSUPPORTED;
@@ -335,8 +432,9 @@ int tc_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0,
   PURL_TRY(make_map(&ma, A, a_r0 + K, a_c0 + M, TC_BM));
   PURL_TRY(make_map(&mb, B, b_r0 + K, b_c0 + N, BN));
   TcView va{a_r0, a_c0}, vb{b_r0, b_c0};
+  const uint32_t idesc = A.f16 ? idesc_f16(TC_BM, BN) : idesc_bf16(TC_BM, BN);
 #define PURL_TC_CASE(BN_, S_) \
-  if (BN == BN_ && S == S_) return launch_tc<BN_, S_>(ma, mb, va, vb, M, N, K, k_chunk, splits, ep, di->ctrl, s);
+  if (BN == BN_ && S == S_) return launch_tc<BN_, S_>(ma, mb, va, vb, M, N, K, k_chunk, splits, ep, di->ctrl, idesc, s);
   PURL_TC_CASE(32, 1) PURL_TC_CASE(64, 1) PURL_TC_CASE(128, 1) PURL_TC_CASE(256, 1)
   PURL_TC_CASE(32, 2) PURL_TC_CASE(64, 2) PURL_TC_CASE(128, 2) PURL_TC_CASE(256, 2)
   PURL_TC_CASE(32, 3) PURL_TC_CASE(64, 3) PURL_TC_CASE(128, 3)
@@ -412,7 +510,8 @@ int noalloc_launch(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, i
                  (double)S * 2.0 * ((double)M * K + (double)N * K) + 8.0 * M * N * (ep.beta != 0.0 ? 2 : 1),
                  "tc noalloc");
   tc_gemm_kernel<BN, S><<<dim3((unsigned)tiles, 1), TC_THREADS, Cfg::SMEM, s>>>(ma, mb, v0, v0, M, N, K,
-                                                                                 ceil_div(K, TC_BK) * TC_BK, ep, ctrl);
+                                                                                 ceil_div(K, TC_BK) * TC_BK, ep, ctrl,
+                                                                                 idesc_bf16(TC_BM, BN));
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 

@@ -26,6 +26,7 @@ struct Slices {
   long long ld = 0;     // elements, multiple of 64
   long long plane = 0;  // elements between slices
   int S = 1;            // slices present
+  int f16 = 0;          // element type of plain slices: 0 BF16, 1 FP16 (same 16-bit storage)
 };
 
 inline long long slice_ld(int rows) { return ((long long)(rows > 0 ? rows : 1) + 63) / 64 * 64; }
@@ -86,6 +87,15 @@ int tcx_gemm_all_pairs(const Slices &A, int a_r0, int a_c0, const Slices &B, int
 // split_slices_t: transposed (dst is Cc x R).
 int split_slices(int R, int Cc, const double *X, long long ldx, Slices dst, cudaStream_t s);
 int split_slices_t(int R, int Cc, const double *X, long long ldx, Slices dst, cudaStream_t s);
+
+// One plain slice (BF16, or FP16 when dst.f16) of 2^s X, with the power of two
+// 2^s chosen on the device from the largest exponent in X so that the largest
+// entry lands just below 2^15 (FP16) or 2 (BF16): the 16-bit formats' range
+// then holds X whatever its magnitude.  The scale is not undone -- callers
+// use it where only the span of the product matters (the power iterates are
+// orthonormalised afterwards).  `e_ws`: one device int of scratch.
+int split_scaled(int R, int Cc, const double *X, long long ldx, Slices dst, int *e_ws, bool transposed,
+                 cudaStream_t s);
 
 // D(M x N) = sum over slice pairs of A_s (M x K) B_t^T (N x K).  A: slices with
 // cols = M, rows = K; B: cols = N, rows = K.  Split-K: `splits` chunks of

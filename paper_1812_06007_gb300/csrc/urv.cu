@@ -62,6 +62,7 @@ struct UrvWork {
   QrMixWork qm;
   Slices At1, An1, Ax, Ys, Zs, Vx;
   Slices Ae, Ze;  // FP64 emulation: A (m x n, scale per column), Z (m x n)
+  int *pexp = nullptr;  // mixed modes: exponent scratch of the scaled power-step slices
 };
 
 // FP64 emulation: every product, including the power steps, with
@@ -87,6 +88,8 @@ static int urv_plan(Arena &ar, int m, int n, int mode, UrvWork *w) {
   if (mode == PURL_MODE_FP64) return qr_plan(ar, m, n, mode, &w->qr);
   if (mode == PURL_MODE_FP64_EMU) return urv_plan_emu(ar, m, n, w);
   PURL_TRY(qr_mixed_plan(ar, m, n, kFinalSlices, &w->qm));
+  const int f16 = mode == PURL_MODE_MIXED_FP16;
+  w->pexp = ar.take<int>(1);
   w->At1 = make_slices(ar.take<__nv_bfloat16>(slice_elems(n, m, 1)), n, m, 1);
   w->An1 = make_slices(ar.take<__nv_bfloat16>(slice_elems(m, n, 1)), m, n, 1);
   w->Ax = make_slices(ar.take<__nv_bfloat16>(slice_elems(n, m, kFinalSlices)), n, m, kFinalSlices);
@@ -95,11 +98,13 @@ static int urv_plan(Arena &ar, int m, int n, int mode, UrvWork *w) {
   w->Zs = make_slices(ar.take<__nv_bfloat16>(slice_elems(m, n, 1)), m, n, 1);
   w->Vx = make_slices(ar.take<__nv_bfloat16>(slice_elems(n, n, kFinalSlices)), n, n, kFinalSlices);
   w->Vx.scale = ar.take<int>(n > 0 ? n : 1);
+  w->At1.f16 = w->An1.f16 = w->Ys.f16 = w->Zs.f16 = f16;
   return PURL_OK;
 }
 
 static bool mode_ok(int mode) {
-  return mode == PURL_MODE_FP64 || mode == PURL_MODE_MIXED_BF16 || mode == PURL_MODE_FP64_EMU;
+  return mode == PURL_MODE_FP64 || mode == PURL_MODE_MIXED_BF16 || mode == PURL_MODE_MIXED_FP16 ||
+         mode == PURL_MODE_FP64_EMU;
 }
 
 // The FP64-emulation products reduce over at most 2^20 rows (their 64-bit
@@ -164,10 +169,15 @@ static int urv_run_fp64(int m, int n, const double *A, int lda, int q, int reort
   return qr_sign_fix(m, n, F, m, U, ldu, R, ldr, s);
 }
 
-// Mixed precision: power steps on BF16 tensor cores (one slice, FP32
-// accumulation -- they only shape the subspace), re-orthonormalisations with
-// kReorthSlices exact slices, and the QRs of Eqs. (5)-(6) plus A V with
-// kFinalSlices exact slices; Householder panels in FP64.
+// Mixed precision: power steps on the tensor cores with one plain BF16 or
+// FP16 slice per operand and FP32 accumulation (they only shape the subspace),
+// re-orthonormalisations with kReorthSlices exact slices, and the QRs of
+// Eqs. (5)-(6) plus A V with kFinalSlices exact slices; Householder panels in
+// FP64.  Every power-step operand is sliced as 2^s X with a power of two
+// chosen from its largest entry (FP16's range is narrow, and the FP32 sums
+// must not overflow); the scale is never undone, since each product is
+// orthonormalised next (with reorth) or only its span enters the QR of
+// Eq. (5) (without), and a positive scale changes neither.
 static int urv_run_mixed(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
                          double *U, int ldu, double *R, int ldr, double *V, int ldv, UrvWork &w,
                          cudaStream_t s) {
@@ -175,12 +185,12 @@ static int urv_run_mixed(int m, int n, const double *A, int lda, int q, int reor
   TcEpilogue ep;
   ep.mode = 0;
   if (q > 0) {
-    PURL_TRY(split_slices_t(m, n, A, lda, w.At1, s));  // operand of A Y   (rows n = K, cols m = M)
-    PURL_TRY(split_slices(m, n, A, lda, w.An1, s));    // operand of A^T Z (rows m = K, cols n = M)
+    PURL_TRY(split_scaled(m, n, A, lda, w.At1, w.pexp, true, s));   // operand of A Y   (rows n = K, cols m = M)
+    PURL_TRY(split_scaled(m, n, A, lda, w.An1, w.pexp, false, s));  // operand of A^T Z (rows m = K, cols n = M)
   }
   PURL_TRY(launch_gaussian(seed, 0, n, n, Y, n, s));
   for (int i = 1; i <= q; ++i) {
-    PURL_TRY(split_slices(n, n, Y, n, w.Ys, s));
+    PURL_TRY(split_scaled(n, n, Y, n, w.Ys, w.pexp, false, s));
     ep.C = F;
     ep.ldc = m;
     PURL_TRY(tc_gemm(w.At1, w.Ys, m, n, n, 1, ep, 1, ceil_div(n, 64) * 64, s));  // F = A Y
@@ -192,7 +202,7 @@ static int urv_run_mixed(int m, int n, const double *A, int lda, int q, int reor
     } else {
       double *t = F; F = Z; Z = t;
     }
-    PURL_TRY(split_slices(m, n, Z, m, w.Zs, s));
+    PURL_TRY(split_scaled(m, n, Z, m, w.Zs, w.pexp, false, s));
     ep.C = F;
     ep.ldc = n;
     PURL_TRY(tc_gemm(w.An1, w.Zs, n, n, m, 1, ep, 1, ceil_div(m, 64) * 64, s));  // F = A^T Z
@@ -288,7 +298,7 @@ static int urv_run_emu(int m, int n, const double *A, int lda, int q, int reorth
 static int urv_run(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
                    double *U, int ldu, double *R, int ldr, double *V, int ldv, int mode,
                    UrvWork &w, cudaStream_t s) {
-  if (mode == PURL_MODE_MIXED_BF16)
+  if (mode == PURL_MODE_MIXED_BF16 || mode == PURL_MODE_MIXED_FP16)
     return urv_run_mixed(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, w, s);
   if (mode == PURL_MODE_FP64_EMU)
     return urv_run_emu(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, w, s);

@@ -60,7 +60,7 @@ def test_argument_errors_are_reported_before_device_work(purl):
     assert L.purl_urv_factor(4, 4, fake, 4, -2, 1, 7, fake, 4, fake, 4, fake, 4, nul) == -5
     assert L.purl_urv_factor(4, 4, fake, 4, 1, 1, 7, fake, 4, fake, 3, fake, 4, nul) == -11
     assert L.purl_urv_factor_ex(4, 4, fake, 4, 1, 1, 7, fake, 4, fake, 4, fake, 4, 99, nul, 0, nul) == -14
-    assert L.purl_urv_factor_ex(4, 4, fake, 4, 1, 1, 7, fake, 4, fake, 4, fake, 4, 3, nul, 0, nul) == -14
+    assert L.purl_urv_factor_ex(4, 4, fake, 4, 1, 1, 7, fake, 4, fake, 4, fake, 4, 5, nul, 0, nul) == -14
     # the FP64-emulation mode reduces over at most 2^20 rows: refused before any device work
     big = (1 << 20) + 1
     assert L.purl_urv_factor_ex(big, 4, fake, big, 1, 1, 7, fake, big, fake, 4, fake, 4, 4, nul, 0, nul) == \

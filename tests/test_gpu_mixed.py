@@ -65,10 +65,12 @@ def test_mixed_qr_matches_oracle(B, m, n):
     (2048, 1024, 2, True, "exponential"),
     (96, 96, 3, True, "step"),
 ])
-def test_mixed_urv_invariants_and_diagonal(B, m, n, q, reorth, profile):
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_mixed_urv_invariants_and_diagonal(B, m, n, q, reorth, profile, fmt):
     sig = W.sigma_profile(profile, n, decades=6)
     A = W.test_matrix_np(m, n, sig)
-    U, R, V = (_host(x) for x in B.purl_urv_factor(_dev(A), q, reorth, W.SEED_G, mode=B.PURL_MODE_MIXED_BF16))
+    mode = B.PURL_MODE_MIXED_BF16 if fmt == "bf16" else B.PURL_MODE_MIXED_FP16
+    U, R, V = (_host(x) for x in B.purl_urv_factor(_dev(A), q, reorth, W.SEED_G, mode=mode))
     nA = np.linalg.norm(A)
     recon = np.linalg.norm(A - U @ R @ V.T) / nA
     ou = np.linalg.norm(U.T @ U - np.eye(n), 2)
@@ -77,7 +79,7 @@ def test_mixed_urv_invariants_and_diagonal(B, m, n, q, reorth, profile):
     d, do = np.abs(np.diag(R)), np.abs(np.diag(Ro))
     lead = sig / sig[0] > 1e-2
     dev = np.abs(d[lead] - do[lead]) / do[lead]
-    print(f"\nmixed {m}x{n} q={q} reorth={reorth} {profile}: recon={recon:.2e} orthU_2={ou:.2e} orthV_2={ov:.2e} "
+    print(f"\nmixed-{fmt} {m}x{n} q={q} reorth={reorth} {profile}: recon={recon:.2e} orthU_2={ou:.2e} orthV_2={ov:.2e} "
           f"|Rjj| rel dev (sigma>1e-2): median={np.median(dev):.2e} max={dev.max():.2e}")
     assert recon <= 1e-6 and ou <= 1e-6 and ov <= 1e-6
     assert np.array_equal(np.tril(R, -1), np.zeros((n, n)))

@@ -9,7 +9,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["fp64", "mixed", "emu"]
+MODES = ["fp64", "mixed", "mixed16", "emu"]
 
 
 @pytest.fixture(scope="module")
@@ -20,7 +20,8 @@ def B():
 
 
 def _mode(B, name):
-    return {"fp64": B.PURL_MODE_FP64, "mixed": B.PURL_MODE_MIXED_BF16, "emu": B.PURL_MODE_FP64_EMU}[name]
+    return {"fp64": B.PURL_MODE_FP64, "mixed": B.PURL_MODE_MIXED_BF16, "mixed16": B.PURL_MODE_MIXED_FP16,
+            "emu": B.PURL_MODE_FP64_EMU}[name]
 
 
 def _dev(B, x):
@@ -57,11 +58,11 @@ def test_factor_reports_nonfinite_and_returns_nan(B, mode, bad):
 
 @pytest.mark.parametrize("mode", MODES)
 def test_large_finite_entries_pass(B, mode):
-    # large finite entries: no status, finite factors.  The mixed mode's power
-    # steps take A as plain BF16 with FP32 sums, so its range is FP32's; the
-    # Householder norms are plain sums of squares, so the other modes take
-    # entries whose squares stay in the FP64 range.
-    scale = 1e30 if mode == "mixed" else 1e100
+    # large finite entries: no status, finite factors.  The mixed modes slice
+    # their power-step operands with a power-of-two scale, so BF16's and
+    # FP16's narrow ranges do not limit A; the Householder norms are plain
+    # sums of squares, so entries are kept where their squares fit in FP64.
+    scale = 1e100
     A = _matrix(72, 64) * scale
     U, R, V = B.purl_urv_factor(_dev(B, A), 1, True, 7, mode=_mode(B, mode))
     assert B.purl_device_status() == B.PURL_OK
