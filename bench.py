@@ -78,7 +78,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip per-kernel event timing")
-    ap.add_argument("--workload", choices=["urv", "batched", "adjoint", "rsvd"], default="urv")
+    ap.add_argument("--workload", choices=["urv", "batched", "adjoint", "rsvd", "product"], default="urv")
+    ap.add_argument("--engine", choices=["f64", "tc", "tcx"], default="tcx",
+                    help="product: FP64 DFMA engine, plain BF16 slices (tc), or exact slices (tcx)")
+    ap.add_argument("--slices", type=int, default=4, help="product: slices per operand")
     ap.add_argument("--matrix", choices=["haar", "gaussian"], default="haar",
                     help="urv: Haar-factor matrix with sigma_j = 10^(-6(j-1)/(n-1)), or Gaussian entries")
     ap.add_argument("--rank", type=int, default=256, help="rsvd: target rank l")
@@ -1113,8 +1116,74 @@ def run_rsvd_reference(a):
     return 0
 
 
+# ------------------------------------------------------------- product -----
+def run_product(a):
+    """One product engine on its own (the a2/a3/a6 products of Section 3): C = A B with m = n = k = a.n,
+    FP64 operands resident on the device, the engine chosen by --engine.  Used for per-engine rooflines
+    and ncu captures; not a PowerURV metric."""
+    import torch
+    from paper_1812_06007_gb300 import binding as B
+    from paper_1812_06007_gb300 import build as Bld
+    Bld.build()
+    B.lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = a.n
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    A = torch.randn(n, n, generator=g, device=dev, dtype=torch.float64).t()
+    Bm = torch.randn(n, n, generator=g, device=dev, dtype=torch.float64).t()
+    C = B.empty_colmajor(n, n, dev)
+    stream = torch.cuda.current_stream()
+    S = a.slices
+
+    def step():
+        if a.engine == "f64":
+            B.purl_gemm_f64("N", "N", A, Bm, C=C, stream=stream)
+        else:
+            B.purl_gemm_tc("N", "N", A, Bm, C=C, slices=S, exact=(a.engine == "tcx"), stream=stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    B.purl_profile_reset()
+    B.purl_profile_set_stride(1)
+    B.purl_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        e0.record(stream)
+        for _ in range(a.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    named = B.purl_profile_read_named()
+    B.purl_profile_enable(False)
+    ms = e0.elapsed_time(e1) / a.steps
+    clocks = clk.summary()
+    roof = roofline(None, named, a.steps, a.engine, sm_mhz=clocks.get("sm_mhz"),
+                    sms=torch.cuda.get_device_properties(dev).multi_processor_count)
+    if roof is not None:
+        attach_traffic(roof)
+    err = None
+    if n <= 8192:
+        ref = A @ Bm
+        err = float((C - ref).abs().max() / (A.abs() @ Bm.abs()).max())
+    line = {"metric": f"product C = A B ({a.engine}, slices={S if a.engine != 'f64' else 0})", "value": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+            "dtype": "f64" if a.engine == "f64" else "bf16 slices",
+            "config": {"workload": f"product m=n=k={n} engine={a.engine} slices={S}",
+                       "l2": f"operands larger than L2 ({8 * n * n / 2**20:.0f} MiB each)" if 8 * n * n > 129e6
+                       else "operands fit in L2"},
+            "max_rel_err": err, "clocks": clocks, "roofline": roof,
+            "kernels_ms_per_step": {k: v["ms"] / a.steps for k, v in named.items()}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = parse()
+    if a.workload == "product":
+        return run_product(a)
     if a.workload == "batched":
         return run_batched_reference(a) if a.impl == "reference" else run_batched(a)
     if a.workload == "adjoint":
