@@ -501,7 +501,10 @@ int split_exact(int R, int Cc, const double *X, long long ldx, Slices dst, const
   if (!di) return PURL_ERR_CUDA;
   if (Cc <= 0) return PURL_OK;
   if (!scale_from && !dst.scale) return PURL_ERR_UNSUPPORTED;
-  int grid = Cc < di->num_sms * 32 ? Cc : di->num_sms * 32;
+  // a block reads its column twice (maximum, then digits): at most 4 columns
+  // per SM in flight keep the second read in L2 for tall columns
+  const int cap = R > 4096 ? di->num_sms * 4 : di->num_sms * 32;
+  int grid = Cc < cap ? Cc : cap;
   LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc, "split_exact_kernel");
   split_exact_kernel<<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;

@@ -134,18 +134,25 @@ __global__ void __launch_bounds__(256) reduce_tmul_slices_kernel(int bw, int nc,
     if (r < bw) mx = max(mx, abs_bits(t));
   }
   mxs[ry][cx] = mx;
-  __syncthreads();
-  unsigned long long m = 0;
+  __syncthreads();  // every thread is done reading the sums in ws
 #pragma unroll
-  for (int y = 0; y < 8; ++y) m = max(m, mxs[y][cx]);
-  const int e = exp_above_bits(m);
-  if (c >= nc) return;
-  if (ry == 0) W2s.scale[c] = e;
+  for (int q = 0; q < 4; ++q) ws[ry + 8 * q][cx] = w2[q];  // ws now holds W2 (rows x 32 columns)
+  __shared__ int es[32];
+  if (ry == 0) {
+    unsigned long long m = 0;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int r = ry + 8 * q;
-    if (r < bw) write_fixed_slices(w2[q], e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
+    for (int y = 0; y < 8; ++y) m = max(m, mxs[y][cx]);
+    es[cx] = exp_above_bits(m);
+    if (c < nc) W2s.scale[c] = es[cx];
   }
+  __syncthreads();
+  // digits written with the lanes along the rows of W2: coalesced per slice
+  const int r = threadIdx.x & 31;
+  if (r < bw)
+    for (int cc = threadIdx.x >> 5; cc < 32; cc += 8) {
+      const int col = blockIdx.x * 32 + cc;
+      if (col < nc) write_fixed_slices(ws[r][cc], es[cc], W2s.base + r + (long long)col * W2s.ld, W2s.plane, W2s.S);
+    }
 }
 
 // Explicit rounded V of an outer block: column t (0 <= t < nbw) of the block
@@ -210,16 +217,36 @@ __global__ void __launch_bounds__(256) reduce_slices_kernel(int nbw, int nc, int
     }
   mxs[ry][cx] = mx;
   __syncthreads();
-  unsigned long long m = 0;
+  __shared__ int es[32];
+  __shared__ double tile[32][33];
+  if (ry == 0) {
+    unsigned long long m = 0;
 #pragma unroll
-  for (int y = 0; y < 8; ++y) m = max(m, mxs[y][cx]);
-  const int e = exp_above_bits(m);
-  if (c >= nc) return;
-  if (ry == 0) W2s.scale[c] = e;
-  for (int r = ry; r < nbw; r += 8) {
-    double a = 0.0;
-    for (int z = 0; z < splits; ++z) a += Pd[(long long)z * nc * nbw + c + (long long)r * nc];
-    write_fixed_slices(a, e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
+    for (int y = 0; y < 8; ++y) m = max(m, mxs[y][cx]);
+    es[cx] = exp_above_bits(m);
+    if (c < nc) W2s.scale[c] = es[cx];
+  }
+  // 32-row chunks: sums read with the lanes along the columns (coalesced
+  // partials), digits written with the lanes along the rows (coalesced slices)
+  for (int r0 = 0; r0 < nbw; r0 += 32) {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + ry + 8 * q;
+      double a = 0.0;
+      if (c < nc && r < nbw)
+        for (int z = 0; z < splits; ++z) a += Pd[(long long)z * nc * nbw + c + (long long)r * nc];
+      tile[ry + 8 * q][cx] = a;
+    }
+    __syncthreads();
+    const int r = r0 + (threadIdx.x & 31);
+    if (r < nbw)
+      for (int cc = threadIdx.x >> 5; cc < 32; cc += 8) {
+        const int col = blockIdx.x * 32 + cc;
+        if (col < nc)
+          write_fixed_slices(tile[threadIdx.x & 31][cc], es[cc], W2s.base + r + (long long)col * W2s.ld, W2s.plane,
+                             W2s.S);
+      }
   }
 }
 

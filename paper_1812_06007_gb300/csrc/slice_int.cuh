@@ -45,29 +45,35 @@ __device__ __forceinline__ long long fixed_point(double x, int e, int P) {
   return (b >> 63) ? -n : n;
 }
 
-// Exact BF16 bit pattern of a small integer |d| <= 256.
-__device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
-  if (d == 0) return 0;
-  const unsigned sgn = d < 0 ? 0x8000u : 0u;
-  const unsigned a = (unsigned)(d < 0 ? -d : d);
-  const int msb = 31 - __clz(a);
-  const unsigned mant = (a << (7 - msb)) & 0x7Fu;
-  return (unsigned short)(sgn | ((unsigned)(127 + msb) << 7) | mant);
+// BF16 bit pattern of a small integer |d| <= 255: its FP32 conversion is
+// exact and has no significant bits below the top 8, so the upper half of the
+// FP32 bits is the BF16 value.
+__device__ __forceinline__ unsigned short bf16_bits_small(int d) {
+  return (unsigned short)(__float_as_uint(__int2float_rn(d)) >> 16);
 }
 
 // Write the S digits of x (|x| < 2^e) as BF16 slices: slice s at dst[s * plane],
-// S <= 8 (P = 7 + 8(S-1) <= 63 keeps N in a 64-bit integer).
+// S <= 8 (P = 7 + 8(S-1) <= 63 keeps N in a 64-bit integer).  The balanced
+// base-256 digits of N are read off M = N + 128 (1 + 2^8 + ... + 2^(8(S-2))):
+// byte j of M minus 128 is the digit of weight 2^(8j) for j < S-1, and M
+// shifted right (arithmetically) by 8(S-1) is the top digit -- the same
+// digits as peeling them off one at a time from the bottom.  M is formed
+// modulo 2^64 (for S = 8 it can pass 2^63), so the top digit t in [-128, 128]
+// is read from its byte, which leaves only t = +-128 ambiguous; N's sign
+// settles that.
 __device__ __forceinline__ void write_fixed_slices(double x, int e, __nv_bfloat16 *dst, long long plane, int S) {
-  long long n = fixed_point(x, e, 7 + 8 * (S - 1));
-  unsigned short digit[8];
-  for (int s = S - 1; s >= 1; --s) {
-    const long long d = ((n + 128) & 255) - 128;
-    digit[s] = bf16_bits_of_int((int)d);
-    n = (n - d) >> 8;
-  }
-  digit[0] = bf16_bits_of_int((int)n);
+  const long long n = fixed_point(x, e, 7 + 8 * (S - 1));
+  const unsigned long long bias = 0x0080808080808080ULL >> (8 * (8 - S));
+  const unsigned long long M = (unsigned long long)n + bias;
   unsigned short *out = reinterpret_cast<unsigned short *>(dst);
-  for (int s = 0; s < S; ++s) out[s * plane] = digit[s];
+  int t = (int)((M >> (8 * (S - 1))) & 255u);
+  t = t >= 128 ? t - 256 : t;
+  if (t == -128 && n > 0) t = 128;
+  out[0] = bf16_bits_small(t);
+  for (int s = 1; s < S; ++s) {
+    const int j = S - 1 - s;  // byte of M that holds slice s
+    out[s * plane] = bf16_bits_small((int)((M >> (8 * j)) & 255u) - 128);
+  }
 }
 
 // The FP64 value of f * 2^k for a finite FP32 f, assembled from the bits of f

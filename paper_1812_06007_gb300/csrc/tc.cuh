@@ -29,7 +29,13 @@ struct Slices {
   int f16 = 0;          // element type of plain slices: 0 BF16, 1 FP16 (same 16-bit storage)
 };
 
-inline long long slice_ld(int rows) { return ((long long)(rows > 0 ? rows : 1) + 63) / 64 * 64; }
+// Leading dimension of a slice plane: rows rounded up to 64 elements, plus 64
+// more when that is a multiple of 512 (1 KB): the rows of a TMA box are then
+// not a large power of two apart, which would map them onto the same L2 sets.
+inline long long slice_ld(int rows) {
+  const long long ld = ((long long)(rows > 0 ? rows : 1) + 63) / 64 * 64;
+  return (ld % 512) == 0 ? ld + 64 : ld;
+}
 inline size_t slice_elems(int rows, int cols, int S) {
   return (size_t)slice_ld(rows) * (size_t)(cols > 0 ? cols : 1) * (size_t)S;
 }
