@@ -58,6 +58,14 @@ extern "C" {
 
 /* precision modes for purl_urv_factor_ex / purl_qr */
 #define PURL_MODE_FP64 0
+/* FP32 precision on the tensor cores: the FP64 mode's algorithm with every
+ * product (A Y, A^T Z, A V, every QR trailing update, Gram matrix and Q
+ * formation) an exact-accumulation product of 3 fixed-point BF16 slices per
+ * operand (every operand row carried to 2^-24 of its scale, FP32's
+ * significand); Householder panels and T factors in FP64.  The precision the
+ * FP32 entry points (purl_urv_factor_f32, purl_urv_backward_f32) use by
+ * default. */
+#define PURL_MODE_FP32 1
 /* Power-step products A Y and A^T Z on BF16 tensor cores with FP32
  * accumulation (one plain BF16 slice per operand, scaled as described under
  * PURL_MODE_MIXED_FP16); A V, every QR trailing update,
@@ -185,6 +193,48 @@ int purl_urv_backward(int m, int n, const double *A, int lda, int q, int reorth,
                       const double *Vbar, int ldvb, double *Abar, int ldab, void *workspace,
                       size_t workspace_bytes, cudaStream_t stream);
 size_t purl_urv_backward_workspace_bytes(int m, int n, int q);
+
+/*
+ * purl_urv_backward_ex -- purl_urv_backward with a precision `mode` for the
+ * recomputed forward pass and every product of the reverse sweep (the paper
+ * defines no derivative; the chain rule is the one stated above):
+ *   PURL_MODE_FP64      FP64 DFMA products, FP64 Householder QRs (as
+ *                       purl_urv_backward);
+ *   PURL_MODE_FP64_EMU  every product an 8-slice exact tensor-core product and
+ *                       every QR that of the FP64-emulation mode (FP64
+ *                       accuracy; m <= 2^20, else PURL_ERR_UNSUPPORTED);
+ *   PURL_MODE_FP32      the same with 3 slices (FP32 precision).
+ * The forward pass it differentiates is purl_urv_factor_ex in the same mode.
+ * Workspace: purl_urv_backward_ex_workspace_bytes(m, n, q, mode) bytes, or
+ * NULL to allocate on `stream`.  Errors as purl_urv_backward, -16 for a bad
+ * mode.
+ */
+int purl_urv_backward_ex(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
+                         const double *Ubar, int ldub, const double *Rbar, int ldrb, const double *Vbar,
+                         int ldvb, double *Abar, int ldab, int mode, void *workspace, size_t workspace_bytes,
+                         cudaStream_t stream);
+size_t purl_urv_backward_ex_workspace_bytes(int m, int n, int q, int mode);
+
+/*
+ * FP32 storage.  purl_urv_factor_f32 and purl_urv_backward_f32 take and
+ * return column-major FP32 matrices (device memory, same arguments and errors
+ * as purl_urv_factor_ex and purl_urv_backward_ex, float in place of double).
+ * The inputs are widened to FP64 in the workspace (exactly), the call runs in
+ * `mode` -- PURL_MODE_FP32 for FP32 precision; any mode of the FP64 entry
+ * point is accepted -- and each result is rounded to FP32 once.  Workspace:
+ * the _workspace_bytes query (FP64 copies of the inputs and outputs plus the
+ * inner call's workspace), or NULL to allocate on `stream`.  A mode the
+ * entry point cannot run returns -14 (factor) or -16 (backward).
+ */
+int purl_urv_factor_f32(int m, int n, const float *A, int lda, int q, int reorth, uint64_t seed, float *U,
+                        int ldu, float *R, int ldr, float *V, int ldv, int mode, void *workspace,
+                        size_t workspace_bytes, cudaStream_t stream);
+size_t purl_urv_f32_workspace_bytes(int m, int n, int mode);
+int purl_urv_backward_f32(int m, int n, const float *A, int lda, int q, int reorth, uint64_t seed,
+                          const float *Ubar, int ldub, const float *Rbar, int ldrb, const float *Vbar, int ldvb,
+                          float *Abar, int ldab, int mode, void *workspace, size_t workspace_bytes,
+                          cudaStream_t stream);
+size_t purl_urv_backward_f32_workspace_bytes(int m, int n, int q, int mode);
 
 /*
  * Batched PowerURV in FP32 (Section 3, Eqs. (5)-(6), for many independent

@@ -24,6 +24,7 @@ PURL_ERR_CUDA = 3
 PURL_ERR_NOMEM = 4
 PURL_ERR_UNSUPPORTED = 5
 PURL_MODE_FP64 = 0
+PURL_MODE_FP32 = 1
 PURL_MODE_MIXED_BF16 = 2
 PURL_MODE_MIXED_FP16 = 3
 PURL_MODE_FP64_EMU = 4
@@ -43,6 +44,12 @@ SIGNATURES = {
     "purl_rsvd_workspace_bytes": (_sz, [_i, _i, _i]),
     "purl_urv_backward": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _p, _i, _p, _sz, _p]),
     "purl_urv_backward_workspace_bytes": (_sz, [_i, _i, _i]),
+    "purl_urv_backward_ex": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
+    "purl_urv_backward_ex_workspace_bytes": (_sz, [_i, _i, _i, _i]),
+    "purl_urv_factor_f32": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
+    "purl_urv_f32_workspace_bytes": (_sz, [_i, _i, _i]),
+    "purl_urv_backward_f32": (_i, [_i, _i, _p, _i, _i, _i, _u64, _p, _i, _p, _i, _p, _i, _p, _i, _i, _p, _sz, _p]),
+    "purl_urv_backward_f32_workspace_bytes": (_sz, [_i, _i, _i, _i]),
     "purl_urv_batched_variants": (_i, []),
     "purl_urv_batched_workspace_bytes": (_sz, [_i, _i, _i]),
     "purl_urv_factor_batched": (_i, [_i, _p, _i, _i, _i, _i, _i, _p, _sz, _p]),
@@ -243,6 +250,65 @@ def purl_urv_backward(A, q: int, reorth: bool, seed: int, Ubar, Rbar, Vbar, out=
 
 def purl_urv_backward_workspace_bytes(m: int, n: int, q: int) -> int:
     return int(lib().purl_urv_backward_workspace_bytes(m, n, q))
+
+
+def purl_urv_backward_ex(A, q: int, reorth: bool, seed: int, Ubar, Rbar, Vbar, mode: int = PURL_MODE_FP64,
+                         out=None, workspace=None, stream=None):
+    """Abar for the map A -> (U, R, V) of purl_urv_factor_ex in `mode` (FP64, FP64_EMU or FP32)."""
+    _cuda_check(A, Ubar, Rbar, Vbar)
+    m, n = A.shape
+    Abar = out if out is not None else empty_colmajor(m, n, A.device)
+    _cuda_check(Abar)
+    ws_ptr, ws_bytes = (_ptr(workspace), workspace.numel() * workspace.element_size()) if workspace is not None \
+        else (ctypes.c_void_p(0), 0)
+    st = lib().purl_urv_backward_ex(m, n, _ptr(A), _ld(A), q, int(bool(reorth)), seed, _ptr(Ubar), _ld(Ubar),
+                                    _ptr(Rbar), _ld(Rbar), _ptr(Vbar), _ld(Vbar), _ptr(Abar), _ld(Abar), mode,
+                                    ws_ptr, ws_bytes, _stream(stream))
+    _check("purl_urv_backward_ex", st)
+    return Abar
+
+
+def _f32_check(*ts):
+    torch = _torch()
+    for t in ts:
+        if t is not None and (not t.is_cuda or t.dtype != torch.float32):
+            raise ValueError("expected CUDA float32 tensors")
+
+
+def purl_urv_factor_f32(A, q: int, reorth: bool, seed: int, mode: int = PURL_MODE_FP32, out=None, workspace=None,
+                        stream=None):
+    """(U, R, V) in FP32 for a column-major CUDA float32 A (computed in `mode`, rounded once)."""
+    torch = _torch()
+    _f32_check(A)
+    m, n = A.shape
+    if out is None:
+        U, R, V = (empty_colmajor(r, c, A.device, torch.float32) for r, c in ((m, n), (n, n), (n, n)))
+    else:
+        U, R, V = out
+    _f32_check(U, R, V)
+    ws_ptr, ws_bytes = (_ptr(workspace), workspace.numel() * workspace.element_size()) if workspace is not None \
+        else (ctypes.c_void_p(0), 0)
+    st = lib().purl_urv_factor_f32(m, n, _ptr(A), _ld(A), q, int(bool(reorth)), seed, _ptr(U), _ld(U), _ptr(R),
+                                   _ld(R), _ptr(V), _ld(V), mode, ws_ptr, ws_bytes, _stream(stream))
+    _check("purl_urv_factor_f32", st)
+    return U, R, V
+
+
+def purl_urv_backward_f32(A, q: int, reorth: bool, seed: int, Ubar, Rbar, Vbar, mode: int = PURL_MODE_FP32,
+                          out=None, workspace=None, stream=None):
+    """FP32 Abar for FP32 A and cotangents (computed in `mode`, rounded once)."""
+    torch = _torch()
+    _f32_check(A, Ubar, Rbar, Vbar)
+    m, n = A.shape
+    Abar = out if out is not None else empty_colmajor(m, n, A.device, torch.float32)
+    _f32_check(Abar)
+    ws_ptr, ws_bytes = (_ptr(workspace), workspace.numel() * workspace.element_size()) if workspace is not None \
+        else (ctypes.c_void_p(0), 0)
+    st = lib().purl_urv_backward_f32(m, n, _ptr(A), _ld(A), q, int(bool(reorth)), seed, _ptr(Ubar), _ld(Ubar),
+                                     _ptr(Rbar), _ld(Rbar), _ptr(Vbar), _ld(Vbar), _ptr(Abar), _ld(Abar), mode,
+                                     ws_ptr, ws_bytes, _stream(stream))
+    _check("purl_urv_backward_f32", st)
+    return Abar
 
 
 class BatchItem(ctypes.Structure):

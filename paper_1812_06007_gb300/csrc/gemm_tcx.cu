@@ -34,11 +34,15 @@
 #include <cuda_bf16.h>
 
 #include "profile.cuh"
+#include "qr.cuh"
 #include "tc.cuh"
 #include "tc_ptx.cuh"
 #include "slice_int.cuh"
 
 namespace purl {
+
+int gemm_f64(bool ta, bool tb, int m, int n, int k, double alpha, const double *A, int lda, const double *B, int ldb,
+             double beta, double *C, int ldc, cudaStream_t s);
 
 namespace {
 
@@ -565,6 +569,61 @@ int tcx_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0
 int tcx_gemm_all_pairs(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0, int b_c0, int M, int N, int K,
                        int S, const TcEpilogue &ep, int splits, int k_chunk, cudaStream_t s) {
   return tcx_gemm_view_impl(A, a_r0, a_c0, B, b_r0, b_c0, M, N, K, S, true, ep, splits, k_chunk, s);
+}
+
+// Scratch layout of gemm_exact: slices of op(A) (K x M) and op(B) (K x N), their
+// scales, and an FP64 staging buffer for the transposed operand.
+static void gemm_exact_plan(Arena &ar, int m, int n, int k, int S, Slices *sa, Slices *sb, double **T) {
+  const int kk = k > 0 ? k : 1, mm = m > 0 ? m : 1, nn = n > 0 ? n : 1;
+  *sa = make_slices(ar.take<__nv_bfloat16>(slice_elems(kk, mm, S)), kk, mm, S);
+  *sb = make_slices(ar.take<__nv_bfloat16>(slice_elems(kk, nn, S)), kk, nn, S);
+  sa->scale = ar.take<int>(mm);
+  sb->scale = ar.take<int>(nn);
+  *T = ar.take<double>((size_t)kk * (size_t)(mm > nn ? mm : nn));
+}
+
+size_t gemm_exact_bytes(int m, int n, int k, int S) {
+  Arena ar;
+  Slices sa, sb;
+  double *T;
+  gemm_exact_plan(ar, m, n, k, S, &sa, &sb, &T);
+  return ar.used;
+}
+
+int gemm_exact(bool ta, bool tb, int m, int n, int k, double alpha, const double *A, int lda, const double *B,
+               int ldb, double beta, double *C, int ldc, int S, void *scratch, size_t scratch_bytes,
+               cudaStream_t s) {
+  if ((long long)m * n == 0) return PURL_OK;
+  if (S < 1 || (S > 4 && S != kTcxEmuSlices)) return PURL_ERR_UNSUPPORTED;
+  if (S > 4 && k > (1 << 20)) return PURL_ERR_UNSUPPORTED;
+  if (k == 0) return gemm_f64(false, false, m, n, 0, 0.0, A, lda, B, ldb, beta, C, ldc, s);
+  Arena ar;
+  ar.base = static_cast<char *>(scratch);
+  ar.size = scratch_bytes;
+  Slices sa, sb;
+  double *T;
+  gemm_exact_plan(ar, m, n, k, S, &sa, &sb, &T);
+  if (!ar.ok) return PURL_ERR_NOMEM;
+  // operand rows along the columns of the sliced matrices: op(A)^T (K x M), op(B) (K x N)
+  if (ta) {
+    PURL_TRY(split_exact(k, m, A, lda, sa, nullptr, s));
+  } else {
+    PURL_TRY(transpose_f64(m, k, A, lda, T, k, s));
+    PURL_TRY(split_exact(k, m, T, k, sa, nullptr, s));
+  }
+  if (tb) {
+    PURL_TRY(transpose_f64(n, k, B, ldb, T, k, s));
+    PURL_TRY(split_exact(k, n, T, k, sb, nullptr, s));
+  } else {
+    PURL_TRY(split_exact(k, n, B, ldb, sb, nullptr, s));
+  }
+  TcEpilogue ep;
+  ep.mode = 0;
+  ep.alpha = alpha;
+  ep.beta = beta;
+  ep.C = C;
+  ep.ldc = ldc;
+  return tcx_gemm_view(sa, 0, 0, sb, 0, 0, m, n, k, S, ep, 1, ceil_div(k, 256) * 256, s);
 }
 
 }  // namespace purl

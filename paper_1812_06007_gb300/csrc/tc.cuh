@@ -89,6 +89,15 @@ int tcx_gemm_view(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0
 int tcx_gemm_all_pairs(const Slices &A, int a_r0, int a_c0, const Slices &B, int b_r0, int b_c0, int M, int N,
                        int K, int S, const TcEpilogue &ep, int splits, int k_chunk, cudaStream_t s);
 
+// C = alpha op(A) op(B) + beta C (FP64 operands, column-major) on the exact
+// engine with S slices per operand (1..4 or kTcxEmuSlices), the operand slices
+// and the FP64 staging of a transposed operand carved from `scratch`
+// (gemm_exact_bytes(m, n, k, S) bytes, 256-byte aligned).  k == 0 scales C.
+size_t gemm_exact_bytes(int m, int n, int k, int S);
+int gemm_exact(bool ta, bool tb, int m, int n, int k, double alpha, const double *A, int lda, const double *B,
+               int ldb, double beta, double *C, int ldc, int S, void *scratch, size_t scratch_bytes,
+               cudaStream_t s);
+
 // FP64 -> S BF16 slices.  split_slices: same orientation (dst is R x Cc);
 // split_slices_t: transposed (dst is Cc x R).
 int split_slices(int R, int Cc, const double *X, long long ldx, Slices dst, cudaStream_t s);

@@ -65,10 +65,15 @@ struct UrvWork {
   int *pexp = nullptr;  // mixed modes: exponent scratch of the scaled power-step slices
 };
 
-// FP64 emulation: every product, including the power steps, with
-// kTcxEmuSlices exact slices (every operand row carried to 2^-63 of its scale).
-static int urv_plan_emu(Arena &ar, int m, int n, UrvWork *w) {
-  constexpr int S = kTcxEmuSlices;
+// Slices per operand of the all-exact modes: every product, the power steps
+// included, is an exact-accumulation product of S fixed-point slices.
+constexpr int kFp32Slices = 3;  // 2^-24 of each operand row's scale: FP32's significand
+static int exact_slices(int mode) { return mode == PURL_MODE_FP32 ? kFp32Slices : kTcxEmuSlices; }
+
+// FP64 emulation (S = kTcxEmuSlices, every operand row carried to 2^-63 of its
+// scale) and FP32 (S = kFp32Slices): every product, including the power steps,
+// with S exact slices.
+static int urv_plan_emu(Arena &ar, int m, int n, int S, UrvWork *w) {
   PURL_TRY(qr_mixed_plan(ar, m, n, S, &w->qm));
   w->Ax = make_slices(ar.take<__nv_bfloat16>(slice_elems(n, m, S)), n, m, S);  // A^T: rows of A as operand rows
   w->Ax.scale = ar.take<int>(m > 0 ? m : 1);
@@ -86,7 +91,7 @@ static int urv_plan(Arena &ar, int m, int n, int mode, UrvWork *w) {
   w->finite = ar.take<int>(1);
   for (int i = 0; i < 3; ++i) w->buf[i] = ar.take<double>(mn);
   if (mode == PURL_MODE_FP64) return qr_plan(ar, m, n, mode, &w->qr);
-  if (mode == PURL_MODE_FP64_EMU) return urv_plan_emu(ar, m, n, w);
+  if (mode == PURL_MODE_FP64_EMU || mode == PURL_MODE_FP32) return urv_plan_emu(ar, m, n, exact_slices(mode), w);
   PURL_TRY(qr_mixed_plan(ar, m, n, kFinalSlices, &w->qm));
   const int f16 = mode == PURL_MODE_MIXED_FP16;
   w->pexp = ar.take<int>(1);
@@ -103,8 +108,13 @@ static int urv_plan(Arena &ar, int m, int n, int mode, UrvWork *w) {
 }
 
 static bool mode_ok(int mode) {
-  return mode == PURL_MODE_FP64 || mode == PURL_MODE_MIXED_BF16 || mode == PURL_MODE_MIXED_FP16 ||
-         mode == PURL_MODE_FP64_EMU;
+  return mode == PURL_MODE_FP64 || mode == PURL_MODE_FP32 || mode == PURL_MODE_MIXED_BF16 ||
+         mode == PURL_MODE_MIXED_FP16 || mode == PURL_MODE_FP64_EMU;
+}
+
+// Slices of purl_qr's products in the tensor-core modes.
+static int qr_slices(int mode) {
+  return (mode == PURL_MODE_FP64_EMU || mode == PURL_MODE_FP32) ? exact_slices(mode) : kFinalSlices;
 }
 
 // The FP64-emulation products reduce over at most 2^20 rows (their 64-bit
@@ -239,9 +249,8 @@ static int urv_run_mixed(int m, int n, const double *A, int lda, int q, int reor
 // BF16 slices, each operand row carried to 2^-63 of its scale.  Householder
 // panels, their Gram matrices and the T factors stay in FP64.
 static int urv_run_emu(int m, int n, const double *A, int lda, int q, int reorth, uint64_t seed,
-                       double *U, int ldu, double *R, int ldr, double *V, int ldv, UrvWork &w,
+                       double *U, int ldu, double *R, int ldr, double *V, int ldv, int S, UrvWork &w,
                        cudaStream_t s) {
-  constexpr int S = kTcxEmuSlices;
   double *Y = w.buf[0], *Z = w.buf[1], *F = w.buf[2];
   qr_mixed_use_slices(w.qm, S);
   // A's slices, made once: A^T (rows of A as operand rows, staged in Z) for
@@ -300,8 +309,8 @@ static int urv_run(int m, int n, const double *A, int lda, int q, int reorth, ui
                    UrvWork &w, cudaStream_t s) {
   if (mode == PURL_MODE_MIXED_BF16 || mode == PURL_MODE_MIXED_FP16)
     return urv_run_mixed(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, w, s);
-  if (mode == PURL_MODE_FP64_EMU)
-    return urv_run_emu(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, w, s);
+  if (mode == PURL_MODE_FP64_EMU || mode == PURL_MODE_FP32)
+    return urv_run_emu(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, exact_slices(mode), w, s);
   return urv_run_fp64(m, n, A, lda, q, reorth, seed, U, ldu, R, ldr, V, ldv, w, s);
 }
 
@@ -460,7 +469,7 @@ size_t purl_qr_workspace_bytes(int m, int n, int mode) {
     if (qr_plan(ar, m, n, mode, &w) != PURL_OK) return 0;
   } else {
     QrMixWork w;
-    if (qr_mixed_plan(ar, m, n, mode == PURL_MODE_FP64_EMU ? kTcxEmuSlices : kFinalSlices, &w) != PURL_OK) return 0;
+    if (qr_mixed_plan(ar, m, n, qr_slices(mode), &w) != PURL_OK) return 0;
   }
   return ar.used;
 }
@@ -495,7 +504,7 @@ int purl_qr(int m, int n, const double *M, int ldm, double *Q, int ldq, double *
     PURL_TRY(qr_explicit(m, n, F, m, Q, ldq, R, ldr, mode, w, stream));
   } else {
     QrMixWork w;
-    PURL_TRY(qr_mixed_plan(ar, m, n, mode == PURL_MODE_FP64_EMU ? kTcxEmuSlices : kFinalSlices, &w));
+    PURL_TRY(qr_mixed_plan(ar, m, n, qr_slices(mode), &w));
     if (!ar.ok) return PURL_ERR_NOMEM;
     PURL_TRY(finite_check(m, n, M, ldm, flag, stream));
     PURL_TRY(copy_matrix(m, n, M, ldm, F, m, stream));
@@ -548,9 +557,14 @@ int purl_gemm_tc(char transa, char transb, int m, int n, int k, double alpha, co
   if ((long long)m * n == 0) return PURL_OK;
   if (!device_info()) return PURL_ERR_CUDA;
   if (k == 0) return gemm_f64(false, false, m, n, 0, 0.0, A, lda, B, ldb, beta, C, ldc, stream);
-  size_t ea = slice_elems(k, m, slices), eb = slice_elems(k, n, slices);
-  size_t tmp = exact ? (size_t)k * (size_t)(m > n ? m : n) : 0;  // FP64 transpose staging
-  size_t bytes = sizeof(__nv_bfloat16) * (ea + eb) + sizeof(double) * tmp + sizeof(int) * ((size_t)m + n) + 2048;
+  if (exact) {
+    const size_t need = gemm_exact_bytes(m, n, k, slices);
+    Scratch scratch;
+    PURL_TRY(scratch.acquire(nullptr, 0, need, stream));
+    return gemm_exact(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, scratch.ptr, need, stream);
+  }
+  const size_t ea = slice_elems(k, m, slices), eb = slice_elems(k, n, slices);
+  const size_t bytes = sizeof(__nv_bfloat16) * (ea + eb) + 1024;
   Scratch scratch;
   PURL_TRY(scratch.acquire(nullptr, 0, bytes, stream));
   Arena ar;
@@ -558,37 +572,19 @@ int purl_gemm_tc(char transa, char transb, int m, int n, int k, double alpha, co
   ar.size = bytes;
   Slices sa = make_slices(ar.take<__nv_bfloat16>(ea), k, m, slices);
   Slices sb = make_slices(ar.take<__nv_bfloat16>(eb), k, n, slices);
+  if (!ar.ok) return PURL_ERR_NOMEM;
   TcEpilogue ep;
   ep.mode = 0;
   ep.alpha = alpha;
   ep.beta = beta;
   ep.C = C;
   ep.ldc = ldc;
-  if (!exact) {
-    // operand A: rows K, cols M (K-major); operand B: rows K, cols N
-    if (ta) PURL_TRY(split_slices(k, m, A, lda, sa, stream));
-    else PURL_TRY(split_slices_t(m, k, A, lda, sa, stream));
-    if (tb) PURL_TRY(split_slices_t(n, k, B, ldb, sb, stream));
-    else PURL_TRY(split_slices(k, n, B, ldb, sb, stream));
-    return tc_gemm(sa, sb, m, n, k, slices, ep, 1, ceil_div(k, 64) * 64, stream);
-  }
-  double *T = tmp ? ar.take<double>(tmp) : nullptr;
-  sa.scale = ar.take<int>(m);
-  sb.scale = ar.take<int>(n);
-  if (!ar.ok) return PURL_ERR_NOMEM;
-  if (ta) {
-    PURL_TRY(split_exact(k, m, A, lda, sa, nullptr, stream));
-  } else {
-    PURL_TRY(transpose_f64(m, k, A, lda, T, k, stream));
-    PURL_TRY(split_exact(k, m, T, k, sa, nullptr, stream));
-  }
-  if (tb) {
-    PURL_TRY(transpose_f64(n, k, B, ldb, T, k, stream));
-    PURL_TRY(split_exact(k, n, T, k, sb, nullptr, stream));
-  } else {
-    PURL_TRY(split_exact(k, n, B, ldb, sb, nullptr, stream));
-  }
-  return tcx_gemm_view(sa, 0, 0, sb, 0, 0, m, n, k, slices, ep, 1, ceil_div(k, 256) * 256, stream);
+  // operand A: rows K, cols M (K-major); operand B: rows K, cols N
+  if (ta) PURL_TRY(split_slices(k, m, A, lda, sa, stream));
+  else PURL_TRY(split_slices_t(m, k, A, lda, sa, stream));
+  if (tb) PURL_TRY(split_slices_t(n, k, B, ldb, sb, stream));
+  else PURL_TRY(split_slices(k, n, B, ldb, sb, stream));
+  return tc_gemm(sa, sb, m, n, k, slices, ep, 1, ceil_div(k, 64) * 64, stream);
 }
 
 int purl_urv_truncate(int m, int n, int k, const double *U, int ldu, const double *R, int ldr,
