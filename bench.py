@@ -67,8 +67,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["mixed", "mixed16", "fp64", "fp64emu"], default="mixed",
-                    help="mixed: BF16 power steps; mixed16: FP16 power steps; fp64; fp64emu")
+    ap.add_argument("--mode", choices=["mixed", "mixed16", "fp32", "fp64", "fp64emu"], default="mixed",
+                    help="mixed: BF16 power steps; mixed16: FP16 power steps; fp32: 3 exact slices; fp64; "
+                         "fp64emu.  --workload adjoint: fp32 (the default there), fp64 or fp64emu")
     ap.add_argument("--m", type=int, default=0, help="rows (default n)")
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--q", type=int, default=2)
@@ -240,8 +241,8 @@ def run_ours(a):
     dev = torch.device("cuda", torch.cuda.current_device())
     Bld.build()
     B.lib()
-    mode = {"mixed": B.PURL_MODE_MIXED_BF16, "mixed16": B.PURL_MODE_MIXED_FP16, "fp64": B.PURL_MODE_FP64,
-            "fp64emu": B.PURL_MODE_FP64_EMU}[a.mode]
+    mode = {"mixed": B.PURL_MODE_MIXED_BF16, "mixed16": B.PURL_MODE_MIXED_FP16, "fp32": B.PURL_MODE_FP32,
+            "fp64": B.PURL_MODE_FP64, "fp64emu": B.PURL_MODE_FP64_EMU}[a.mode]
     m, n, q, reorth = a.m, a.n, a.q, a.reorth
 
     if a.matrix == "gaussian":
@@ -305,12 +306,12 @@ def run_ours(a):
 
     # ---- the FP64 path on the same recipe (the "vs FP64" of the metric) ----
     fp64 = fp64emu = None
-    if a.mode in ("mixed", "mixed16", "fp64emu") and (a.fp64_n > 0 or a.fp64emu_n > 0):
+    if a.mode in ("mixed", "mixed16", "fp32", "fp64emu") and (a.fp64_n > 0 or a.fp64emu_n > 0):
         del ws
         torch.cuda.empty_cache()
-    if a.mode in ("mixed", "mixed16", "fp64emu") and a.fp64_n > 0:
+    if a.mode in ("mixed", "mixed16", "fp32", "fp64emu") and a.fp64_n > 0:
         fp64 = fp64_compare(a, dev, B, W, seed, B.PURL_MODE_FP64, a.fp64_n, A)
-    if a.mode in ("mixed", "mixed16") and a.fp64emu_n > 0:
+    if a.mode in ("mixed", "mixed16", "fp32") and a.fp64emu_n > 0:
         fp64emu = fp64_compare(a, dev, B, W, seed, B.PURL_MODE_FP64_EMU, a.fp64emu_n, A)
 
     if rank != 0:
@@ -339,8 +340,8 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "data": "synthetic",
-        "dtype": {"mixed": "bf16+f64", "mixed16": "fp16+bf16+f64", "fp64": "f64",
-                  "fp64emu": "f64 (emulated: 8 bf16 slices, exact sums)"}[a.mode],
+        "dtype": {"mixed": "bf16+f64", "mixed16": "fp16+bf16+f64", "fp32": "f32 (3 bf16 slices, exact sums)",
+                  "fp64": "f64", "fp64emu": "f64 (emulated: 8 bf16 slices, exact sums)"}[a.mode],
         "config": {"workload": f"PowerURV m={m} n={n} q={q} reorth={int(reorth)} {a.mode}",
                    "m": m, "n": n, "q": q, "reorth": reorth, "mode": a.mode,
                    "matrix": ("Gaussian entries" if a.matrix == "gaussian"
@@ -860,7 +861,7 @@ def run_batched_reference(a):
 
 
 # ------------------------------------------------------------- adjoint -----
-ADJOINT_METRIC = "PowerURV adjoint (FP64 reverse mode, G fixed) seconds per backward, m=n=2048 q=2 reorth"
+ADJOINT_METRIC = "PowerURV adjoint (reverse mode, G fixed) seconds per backward, m=n=2048 q=2 reorth"
 
 
 def adjoint_flops(m, n, q, reorth):
@@ -885,18 +886,28 @@ def run_adjoint(a):
     dev = torch.device("cuda", torch.cuda.current_device())
     n = a.n if a.n != 16384 else 2048
     m, q, reorth = (a.m if a.m != a.n else n), a.q, a.reorth
-    A = W.gaussian_matrix_torch(m, n, 2048, device=dev)
+    amode = {"mixed": "fp32", "fp32": "fp32", "fp64": "fp64", "fp64emu": "fp64emu"}.get(a.mode)
+    if amode is None:
+        raise SystemExit("--workload adjoint runs --mode fp32, fp64 or fp64emu")
+    f32 = amode == "fp32"
+    mode = {"fp32": B.PURL_MODE_FP32, "fp64": B.PURL_MODE_FP64, "fp64emu": B.PURL_MODE_FP64_EMU}[amode]
+    dt = torch.float32 if f32 else torch.float64
+    esz = 4 if f32 else 8
+    A = W.gaussian_matrix_torch(m, n, 2048, device=dev).to(dt).t().contiguous().t()
     gen = torch.Generator(device=dev)
     gen.manual_seed(W.SEED_B)
-    Ub = torch.randn(n, m, generator=gen, device=dev, dtype=torch.float64).t()
-    Rb = torch.randn(n, n, generator=gen, device=dev, dtype=torch.float64).t()
-    Vb = torch.randn(n, n, generator=gen, device=dev, dtype=torch.float64).t()
-    ws = torch.empty(B.purl_urv_backward_workspace_bytes(m, n, q), dtype=torch.uint8, device=dev)
-    Ab = B.empty_colmajor(m, n, dev)
+    Ub = torch.randn(n, m, generator=gen, device=dev, dtype=torch.float64).to(dt).t()
+    Rb = torch.randn(n, n, generator=gen, device=dev, dtype=torch.float64).to(dt).t()
+    Vb = torch.randn(n, n, generator=gen, device=dev, dtype=torch.float64).to(dt).t()
+    nbytes = (B.purl_urv_backward_f32_workspace_bytes(m, n, q, mode) if f32 else
+              B.purl_urv_backward_ex_workspace_bytes(m, n, q, mode))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    Ab = B.empty_colmajor(m, n, dev, dt)
     stream = torch.cuda.current_stream()
+    backward = B.purl_urv_backward_f32 if f32 else B.purl_urv_backward_ex
 
     def step():
-        B.purl_urv_backward(A, q, reorth, W.SEED_G, Ub, Rb, Vb, out=Ab, workspace=ws, stream=stream)
+        backward(A, q, reorth, W.SEED_G, Ub, Rb, Vb, mode=mode, out=Ab, workspace=ws, stream=stream)
 
     for _ in range(a.warmup):
         step()
@@ -917,18 +928,18 @@ def run_adjoint(a):
     sec = e0.elapsed_time(e1) / a.steps * 1e-3
     F = adjoint_flops(m, n, q, reorth)
     clocks = clk.summary()
-    roof = roofline(None, named, a.steps, "fp64", sm_mhz=clocks.get("sm_mhz"),
+    roof = roofline(None, named, a.steps, amode, sm_mhz=clocks.get("sm_mhz"),
                     sms=torch.cuda.get_device_properties(dev).multi_processor_count)
     # end to end: A and cotangents from pinned host memory, gradient back
     hA, hU = A.cpu().pin_memory(), Ub.cpu().pin_memory()
     hR, hV, hAb = Rb.cpu().pin_memory(), Vb.cpu().pin_memory(), torch.empty_like(Ab.cpu()).pin_memory()
-    dA, dU, dR, dV = (B.empty_colmajor(*t.shape, dev) for t in (A, Ub, Rb, Vb))
+    dA, dU, dR, dV = (B.empty_colmajor(*t.shape, dev, dt) for t in (A, Ub, Rb, Vb))
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     x0.record(stream)
     for _ in range(max(1, min(a.steps, 3))):
         for d_, h_ in ((dA, hA), (dU, hU), (dR, hR), (dV, hV)):
             d_.copy_(h_, non_blocking=True)
-        B.purl_urv_backward(dA, q, reorth, W.SEED_G, dU, dR, dV, out=Ab, workspace=ws, stream=stream)
+        backward(dA, q, reorth, W.SEED_G, dU, dR, dV, mode=mode, out=Ab, workspace=ws, stream=stream)
         hAb.copy_(Ab, non_blocking=True)
     x1.record(stream)
     torch.cuda.synchronize()
@@ -939,13 +950,16 @@ def run_adjoint(a):
     line = {
         "metric": ADJOINT_METRIC, "value": sec, "unit": "s", "n_gpus": 1, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"PowerURV reverse mode m={m} n={n} q={q} reorth={int(reorth)}, Gaussian A, "
-                               "random cotangents", "m": m, "n": n, "q": q, "reorth": reorth,
+        "vs_baseline": None, "data": "synthetic",
+        "dtype": {"fp32": "f32 (3 bf16 slices, exact sums)", "fp64": "f64",
+                  "fp64emu": "f64 (emulated: 8 bf16 slices, exact sums)"}[amode],
+        "config": {"workload": f"PowerURV reverse mode m={m} n={n} q={q} reorth={int(reorth)} {amode}, "
+                               "Gaussian A, random cotangents", "m": m, "n": n, "q": q, "reorth": reorth,
+                   "mode": amode,
                    "l2": f"working set {8 * (6 * m * n + 12 * n * n) / 2**20:.0f} MiB > L2"},
         "tflops": F / sec / 1e12, "flops_per_step": F, "roofline": roof, "cpu_baseline": cpu,
-        "e2e": {"value": e2e_sec, "unit": "s", "h2d_bytes_per_step": 8 * (2 * m * n + 2 * n * n),
-                "d2h_bytes_per_step": 8 * m * n},
+        "e2e": {"value": e2e_sec, "unit": "s", "h2d_bytes_per_step": esz * (2 * m * n + 2 * n * n),
+                "d2h_bytes_per_step": esz * m * n},
         "gpu_launches": int(launches), "clocks": clocks,
         "kernels_by_name": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / a.steps}
                             for k, v in sorted(named.items(), key=lambda kv: -kv[1]["ms"])[:8]},

@@ -116,10 +116,20 @@ __global__ void __launch_bounds__(256) reduce_tmul_slices_kernel(int bw, int nc,
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int l = ry + 8 * q;
-    double v = 0.0;
-    if (c < nc && l < bw)
-      for (int z = 0; z < splits; ++z) v += Pd[(long long)z * nc * bw + c + (long long)l * nc];
-    ws[l][cx] = v;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;  // independent loads in flight
+    if (c < nc && l < bw) {
+      const double *pz = Pd + c + (long long)l * nc;
+      const long long st = (long long)nc * bw;
+      int z = 0;
+      for (; z + 3 < splits; z += 4) {
+        v0 += pz[z * st];
+        v1 += pz[(z + 1) * st];
+        v2 += pz[(z + 2) * st];
+        v3 += pz[(z + 3) * st];
+      }
+      for (; z < splits; ++z) v0 += pz[z * st];
+    }
+    ws[l][cx] = (v0 + v1) + (v2 + v3);
   }
   __syncthreads();
   double w2[4];
@@ -134,25 +144,18 @@ __global__ void __launch_bounds__(256) reduce_tmul_slices_kernel(int bw, int nc,
     if (r < bw) mx = max(mx, abs_bits(t));
   }
   mxs[ry][cx] = mx;
-  __syncthreads();  // every thread is done reading the sums in ws
-#pragma unroll
-  for (int q = 0; q < 4; ++q) ws[ry + 8 * q][cx] = w2[q];  // ws now holds W2 (rows x 32 columns)
-  __shared__ int es[32];
-  if (ry == 0) {
-    unsigned long long m = 0;
-#pragma unroll
-    for (int y = 0; y < 8; ++y) m = max(m, mxs[y][cx]);
-    es[cx] = exp_above_bits(m);
-    if (c < nc) W2s.scale[c] = es[cx];
-  }
   __syncthreads();
-  // digits written with the lanes along the rows of W2: coalesced per slice
-  const int r = threadIdx.x & 31;
-  if (r < bw)
-    for (int cc = threadIdx.x >> 5; cc < 32; cc += 8) {
-      const int col = blockIdx.x * 32 + cc;
-      if (col < nc) write_fixed_slices(ws[r][cc], es[cc], W2s.base + r + (long long)col * W2s.ld, W2s.plane, W2s.S);
-    }
+  unsigned long long m = 0;
+#pragma unroll
+  for (int y = 0; y < 8; ++y) m = max(m, mxs[y][cx]);
+  const int e = exp_above_bits(m);
+  if (c >= nc) return;
+  if (ry == 0) W2s.scale[c] = e;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = ry + 8 * q;
+    if (r < bw) write_fixed_slices(w2[q], e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
+  }
 }
 
 // Explicit rounded V of an outer block: column t (0 <= t < nbw) of the block
@@ -325,12 +328,18 @@ void splits_for(int M, int N, int K, int num_sms, int *splits, int *chunk) {
   *splits = ceil_div(K, *chunk);
 }
 
+// Buffers of one inner-block update: the panel's V slices (natural and
+// transposed), the split-K partials of W^T = C^T V and the slices of W2.  The
+// look-ahead runs two updates at once, each with its own set.
+struct InnerBufs {
+  Slices Vs, Vts, W2s;
+  double *Pd = nullptr;
+};
+
 // Slices of the panel's V (natural and transposed) from w.base.Vb (rows x bw).
-int slice_panel(int rows, int bw, QrMixWork &w, cudaStream_t s) {
-  const DeviceInfo *di = device_info();
-  (void)di;
+int slice_panel(int rows, int bw, QrMixWork &w, const InnerBufs &b, cudaStream_t s) {
   { LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 4.0 * w.S) * (double)rows * bw, "split_v_kernel");
-    split_v_kernel<<<ceil_div(rows, 32), 256, 0, s>>>(rows, bw, w.base.Vb, rows, w.Vs, w.Vts); }
+    split_v_kernel<<<ceil_div(rows, 32), 256, 0, s>>>(rows, bw, w.base.Vb, rows, b.Vs, b.Vts); }
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
@@ -339,7 +348,7 @@ int slice_panel(int rows, int bw, QrMixWork &w, cudaStream_t s) {
 // column (its current maximum, written to cexp[c0 + c]): an entry's slicing
 // error is then 2^-8S of its column's largest entry, not of the column norm.
 int apply_block_mixed(int rows, int bw, int nc, double *Cp, int ldc, const Slices &Cs, int r0, int c0,
-                      int *cexp, const double *T, bool trans, QrMixWork &w, cudaStream_t s) {
+                      int *cexp, const double *T, bool trans, QrMixWork &w, const InnerBufs &b, cudaStream_t s) {
   if (nc <= 0 || rows <= 0 || bw <= 0) return PURL_OK;
   const DeviceInfo *di = device_info();
   Slices view = Cs;
@@ -351,12 +360,12 @@ int apply_block_mixed(int rows, int bw, int nc, double *Cp, int ldc, const Slice
   splits_for(nc, bw, rows, di->num_sms, &sp, &ch);
   TcEpilogue ep;
   ep.mode = 2;
-  ep.Pd = w.Pd;
+  ep.Pd = b.Pd;
   ep.tag = "tcx inner V^T C";
-  PURL_TRY(tcx_gemm_view(Cs, r0, c0, w.Vs, 0, 0, nc, bw, rows, w.S, ep, sp, ch, s));
+  PURL_TRY(tcx_gemm_view(Cs, r0, c0, b.Vs, 0, 0, nc, bw, rows, w.S, ep, sp, ch, s));
   // W2 = op(T) W, sliced
   { LaunchScope ls(KC_OTHER, s, 2.0 * bw * bw * (double)nc, 8.0 * sp * (double)nc * bw, "reduce_tmul_slices_kernel");
-    reduce_tmul_slices_kernel<<<ceil_div(nc, 32), 256, 0, s>>>(bw, nc, sp, w.Pd, T, trans, w.W2s); }
+    reduce_tmul_slices_kernel<<<ceil_div(nc, 32), 256, 0, s>>>(bw, nc, sp, b.Pd, T, trans, b.W2s); }
   PURL_CUDA_TRY(cudaGetLastError());
   // C <- C - V W2 (FP64)
   TcEpilogue up;
@@ -366,7 +375,7 @@ int apply_block_mixed(int rows, int bw, int nc, double *Cp, int ldc, const Slice
   up.C = Cp;
   up.ldc = ldc;
   up.tag = "tcx inner update";
-  return tcx_gemm_view(w.Vts, 0, 0, w.W2s, 0, 0, rows, nc, bw, w.S, up, 1, kChunkAlign, s);
+  return tcx_gemm_view(b.Vts, 0, 0, b.W2s, 0, 0, rows, nc, bw, w.S, up, 1, kChunkAlign, s);
 }
 
 constexpr int kOuterSplits = 4;
@@ -503,6 +512,13 @@ int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w) {
   w->Pd = ar.take<double>((size_t)QR_MAX_SPLITS * nn * QR_B);
   w->W2s = make_slices(ar.take<__nv_bfloat16>(slice_elems(QR_B, n, S)), QR_B, n, S);
   w->W2s.scale = ar.take<int>(nn);
+  w->Vs2 = make_slices(ar.take<__nv_bfloat16>(slice_elems(m, QR_B, S)), m, QR_B, S);
+  w->Vs2.scale = ar.take<int>(QR_B);
+  w->Vts2 = make_slices(ar.take<__nv_bfloat16>(slice_elems(QR_B, m, S)), QR_B, m, S);
+  w->Vts2.scale = ar.take<int>(mm);
+  w->Pd2 = ar.take<double>((size_t)QR_MAX_SPLITS * nn * QR_B);
+  w->W2s2 = make_slices(ar.take<__nv_bfloat16>(slice_elems(QR_B, n, S)), QR_B, n, S);
+  w->W2s2.scale = ar.take<int>(nn);
   const size_t nout = (size_t)ceil_div(n > 0 ? n : 1, QR_NB);
   w->Tout = ar.take<double>(nout * QR_NB * QR_NB);
   w->Gparts = ar.take<double>((size_t)kGramParts * QR_B * QR_B);
@@ -524,22 +540,62 @@ int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w) {
   return PURL_OK;
 }
 
+// Second stream and two events of the look-ahead, per host thread and device
+// (so concurrent host threads never share them): the lowest priority, so that
+// the panels on the caller's stream are scheduled first.
+struct AuxStream {
+  int device = -1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t go = nullptr, done = nullptr;
+};
+
+int aux_stream(AuxStream **out) {
+  static thread_local AuxStream cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PURL_ERR_CUDA;
+  AuxStream &a = cache[dev];
+  if (a.device != dev) {
+    int lo = 0, hi = 0;
+    PURL_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    PURL_CUDA_TRY(cudaStreamCreateWithPriority(&a.s, cudaStreamNonBlocking, lo));
+    PURL_CUDA_TRY(cudaEventCreateWithFlags(&a.go, cudaEventDisableTiming));
+    PURL_CUDA_TRY(cudaEventCreateWithFlags(&a.done, cudaEventDisableTiming));
+    a.device = dev;
+  }
+  *out = &a;
+  return PURL_OK;
+}
+
+// Blocked factorization with look-ahead inside each outer block.  After panel
+// p's reflectors and T are formed, the caller's stream s updates only the next
+// panel's columns and goes on to factor it, while the auxiliary stream a
+// updates the rest of the outer block:
+//   s:  panel p -> V slices -> T_p -> [wait a(p-1)] update panel p+1's columns -> record go_p -> panel p+1 ...
+//   a:  [wait go_p] update columns beyond panel p+1 -> record done_p
+// Column sets are disjoint at any time; a(p-1) (which updated panel p+1's
+// columns with panel p-1's reflectors) completes before s applies panel p's
+// to them.  The two updates use separate buffer sets; the V slices alternate
+// between them by panel parity.  The outer update waits for a.
 int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t s) {
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
   if (n == 0) return PURL_OK;
+  AuxStream *aux = nullptr;
+  PURL_TRY(aux_stream(&aux));
+  const InnerBufs bufs[2] = {{w.Vs, w.Vts, w.W2s, w.Pd}, {w.Vs2, w.Vts2, w.W2s2, w.Pd2}};
   const int npan = ceil_div(n, QR_B);
   PURL_CUDA_TRY(cudaMemsetAsync(w.base.counters, 0, sizeof(unsigned) * npan, s));
+  bool aux_pending = false;  // work on the auxiliary stream not yet joined into s
   for (int J0 = 0, ob = 0; J0 < n; J0 += QR_NB, ++ob) {
     const int nbw = min(QR_NB, n - J0), rows = m - J0, nc_out = n - J0 - nbw;
-    // inner panels, their updates confined to the outer block's columns
-    for (int j0 = J0; j0 < J0 + nbw; j0 += QR_B) {
+    for (int j0 = J0, k = 0; j0 < J0 + nbw; j0 += QR_B, ++k) {
       const int p = j0 / QR_B, bw = min(QR_B, J0 + nbw - j0), rj = m - j0;
       const int nc_in = J0 + nbw - j0 - bw;
       double *Fp = F + j0 + (size_t)j0 * ldf;
       double *taup = w.base.tau + j0;
+      const InnerBufs &b = bufs[k & 1];
       PURL_TRY(panel_factor(rj, bw, Fp, ldf, taup, w.base.counters + p, w.base, s));
-      PURL_TRY(slice_panel(rj, bw, w, s));
+      PURL_TRY(slice_panel(rj, bw, w, b, s));
       // T_k from the FP64 Gram matrix of the rounded V^ (exact to FP64 rounding)
       int gchunk = ceil_div(ceil_div(rj, kGramParts), 64) * 64;
       if (gchunk < 64) gchunk = 64;
@@ -551,8 +607,30 @@ int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t
       PURL_CUDA_TRY(cudaGetLastError());
       double *Tp = w.base.T + (size_t)p * QR_B * QR_B;
       PURL_TRY(larft_from_gram(bw, 1, w.base.Gp, taup, Tp, s, true));
-      PURL_TRY(apply_block_mixed(rj, bw, nc_in, Fp + (size_t)bw * ldf, ldf, w.Fs, j0, j0 + bw, w.col_exp, Tp, true,
-                                 w, s));
+      if (nc_in <= 0) continue;
+      // the next panel's columns, on s, after the auxiliary stream's previous update of them
+      if (aux_pending) {
+        PURL_CUDA_TRY(cudaStreamWaitEvent(s, aux->done, 0));
+        aux_pending = false;
+      }
+      const int nxt = min(QR_B, nc_in);
+      PURL_TRY(apply_block_mixed(rj, bw, nxt, Fp + (size_t)bw * ldf, ldf, w.Fs, j0, j0 + bw, w.col_exp, Tp, true, w,
+                                 b, s));
+      const int rest = nc_in - nxt;
+      if (rest > 0) {
+        // the rest of the outer block, on the auxiliary stream
+        PURL_CUDA_TRY(cudaEventRecord(aux->go, s));
+        PURL_CUDA_TRY(cudaStreamWaitEvent(aux->s, aux->go, 0));
+        const InnerBufs ba = {b.Vs, b.Vts, bufs[(k + 1) & 1].W2s, bufs[(k + 1) & 1].Pd};
+        PURL_TRY(apply_block_mixed(rj, bw, rest, Fp + (size_t)(bw + nxt) * ldf, ldf, w.Fs, j0, j0 + bw + nxt,
+                                   w.col_exp, Tp, true, w, ba, aux->s));
+        PURL_CUDA_TRY(cudaEventRecord(aux->done, aux->s));
+        aux_pending = true;
+      }
+    }
+    if (aux_pending) {
+      PURL_CUDA_TRY(cudaStreamWaitEvent(s, aux->done, 0));
+      aux_pending = false;
     }
     // one aggregated update of everything to the right of the outer block
     double *Tout = w.Tout + (size_t)ob * QR_NB * QR_NB;
