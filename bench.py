@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["mixed", "mixed16", "fp32", "fp64", "fp64emu"], default="mixed",
-                    help="mixed: BF16 power steps; mixed16: FP16 power steps; fp32: 3 exact slices; fp64; "
+                    help="mixed: BF16 power steps; mixed16: FP16 power steps; fp32: 4 exact slices; fp64; "
                          "fp64emu.  --workload adjoint: fp32 (the default there), fp64 or fp64emu")
     ap.add_argument("--m", type=int, default=0, help="rows (default n)")
     ap.add_argument("--n", type=int, default=16384)
@@ -340,7 +340,7 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "data": "synthetic",
-        "dtype": {"mixed": "bf16+f64", "mixed16": "fp16+bf16+f64", "fp32": "f32 (3 bf16 slices, exact sums)",
+        "dtype": {"mixed": "bf16+f64", "mixed16": "fp16+bf16+f64", "fp32": "f32 (4 bf16 slices, exact sums)",
                   "fp64": "f64", "fp64emu": "f64 (emulated: 8 bf16 slices, exact sums)"}[a.mode],
         "config": {"workload": f"PowerURV m={m} n={n} q={q} reorth={int(reorth)} {a.mode}",
                    "m": m, "n": n, "q": q, "reorth": reorth, "mode": a.mode,
@@ -951,7 +951,7 @@ def run_adjoint(a):
         "metric": ADJOINT_METRIC, "value": sec, "unit": "s", "n_gpus": 1, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "data": "synthetic",
-        "dtype": {"fp32": "f32 (3 bf16 slices, exact sums)", "fp64": "f64",
+        "dtype": {"fp32": "f32 (4 bf16 slices, exact sums)", "fp64": "f64",
                   "fp64emu": "f64 (emulated: 8 bf16 slices, exact sums)"}[amode],
         "config": {"workload": f"PowerURV reverse mode m={m} n={n} q={q} reorth={int(reorth)} {amode}, "
                                "Gaussian A, random cotangents", "m": m, "n": n, "q": q, "reorth": reorth,

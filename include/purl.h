@@ -60,9 +60,10 @@ extern "C" {
 #define PURL_MODE_FP64 0
 /* FP32 precision on the tensor cores: the FP64 mode's algorithm with every
  * product (A Y, A^T Z, A V, every QR trailing update, Gram matrix and Q
- * formation) an exact-accumulation product of 3 fixed-point BF16 slices per
- * operand (every operand row carried to 2^-24 of its scale, FP32's
- * significand); Householder panels and T factors in FP64.  The precision the
+ * formation) an exact-accumulation product of 4 fixed-point BF16 slices per
+ * operand (every operand row carried to 2^-32 of its scale, so entries down to
+ * 2^-8 of their row's largest keep FP32's 24 bits); Householder panels and T
+ * factors in FP64.  The precision the
  * FP32 entry points (purl_urv_factor_f32, purl_urv_backward_f32) use by
  * default. */
 #define PURL_MODE_FP32 1
@@ -203,7 +204,7 @@ size_t purl_urv_backward_workspace_bytes(int m, int n, int q);
  *   PURL_MODE_FP64_EMU  every product an 8-slice exact tensor-core product and
  *                       every QR that of the FP64-emulation mode (FP64
  *                       accuracy; m <= 2^20, else PURL_ERR_UNSUPPORTED);
- *   PURL_MODE_FP32      the same with 3 slices (FP32 precision).
+ *   PURL_MODE_FP32      the same with 4 slices (FP32 precision).
  * The forward pass it differentiates is purl_urv_factor_ex in the same mode.
  * Workspace: purl_urv_backward_ex_workspace_bytes(m, n, q, mode) bytes, or
  * NULL to allocate on `stream`.  Errors as purl_urv_backward, -16 for a bad

@@ -268,6 +268,18 @@ def purl_urv_backward_ex(A, q: int, reorth: bool, seed: int, Ubar, Rbar, Vbar, m
     return Abar
 
 
+def purl_urv_backward_ex_workspace_bytes(m: int, n: int, q: int, mode: int = PURL_MODE_FP64) -> int:
+    return int(lib().purl_urv_backward_ex_workspace_bytes(m, n, q, mode))
+
+
+def purl_urv_f32_workspace_bytes(m: int, n: int, mode: int = PURL_MODE_FP32) -> int:
+    return int(lib().purl_urv_f32_workspace_bytes(m, n, mode))
+
+
+def purl_urv_backward_f32_workspace_bytes(m: int, n: int, q: int, mode: int = PURL_MODE_FP32) -> int:
+    return int(lib().purl_urv_backward_f32_workspace_bytes(m, n, q, mode))
+
+
 def _f32_check(*ts):
     torch = _torch()
     for t in ts:

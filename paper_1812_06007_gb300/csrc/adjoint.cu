@@ -37,7 +37,7 @@ constexpr int kInvBlock = 32;
 // Arithmetic of the products and QRs of one backward call: S = 0 is the FP64
 // path (DFMA products, FP64 Householder QR); S > 0 runs every product on the
 // exact tensor-core engine with S fixed-point slices per operand (8: FP64
-// emulated, 3: FP32 precision) and every QR as the tensor-core QR of the same
+// emulated, 4: FP32 precision) and every QR as the tensor-core QR of the same
 // slice count, so the recomputed forward pass is the forward mode's own.
 struct Eng {
   int S = 0;
@@ -195,7 +195,7 @@ struct BwdPlan {
 int bwd_slices(int mode) {
   if (mode == PURL_MODE_FP64) return 0;
   if (mode == PURL_MODE_FP64_EMU) return kTcxEmuSlices;
-  if (mode == PURL_MODE_FP32) return 3;
+  if (mode == PURL_MODE_FP32) return 4;
   return -1;
 }
 

@@ -2,7 +2,7 @@
 //
 // The entry points take and return FP32 matrices.  Inputs are widened to FP64
 // in the workspace (exactly), the call runs in the requested mode -- by default
-// PURL_MODE_FP32, whose products are 3-slice exact tensor-core products (FP32
+// PURL_MODE_FP32, whose products are 4-slice exact tensor-core products (FP32
 // precision) -- and the FP64 results are rounded to FP32 once.
 #include "common.cuh"
 #include "profile.cuh"

@@ -304,8 +304,22 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
       for (int j = 0; j < NA; ++j) hi[j] = lo[j] = 0.0f;
 #pragma unroll
       for (int j = 0; j < NW; ++j) accH[j] = accL[j] = 0;
+      // the first batch of C is loaded before the wait for the tile's last
+      // chunk, so its latency runs under that chunk's products
+      constexpr int BATCH = Cfg::WIDE ? 8 : 16;  // independent loads of C kept in flight
+      constexpr int PRE = 8;                      // of which loaded early
+      double cpre[PRE];
+#pragma unroll
+      for (int jj = 0; jj < PRE; ++jj) cpre[jj] = 0.0;
       for (int c = 0; c < nch; ++c, ++ct) {
         const int b = (int)(ct & 1);
+        if (c == nch - 1 && reads_c && row < M) {
+#pragma unroll
+          for (int jj = 0; jj < PRE; ++jj) {
+            const int col = n0 + cbase + jj;
+            cpre[jj] = (col < N) ? __ldcg(ep.C + row + (long long)col * ep.ldc) : 0.0;
+          }
+        }
         if (!mbar_wait(&tfull_bar[b], (uint32_t)(ct >> 1) & 1u, ctrl, &s_abort)) {
           ok = false;
           break;
@@ -356,14 +370,14 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
         const bool plain = (ep.alpha == 1.0 && ep.beta == 0.0);
         const bool subtract = (ep.alpha == -1.0 && ep.beta == 1.0);
         const int z = (int)(work / tiles);
-        constexpr int BATCH = Cfg::WIDE ? 8 : 16;  // independent loads of C kept in flight
 #pragma unroll
         for (int j0 = 0; j0 < HC; j0 += BATCH) {
           double cv[BATCH];
 #pragma unroll
           for (int jj = 0; jj < BATCH; ++jj) {
             const int col = n0 + cbase + j0 + jj;
-            cv[jj] = (reads_c && col < N) ? __ldcg(ep.C + row + (long long)col * ep.ldc) : 0.0;
+            cv[jj] = (j0 == 0 && jj < PRE) ? cpre[jj]
+                                           : ((reads_c && col < N) ? __ldcg(ep.C + row + (long long)col * ep.ldc) : 0.0);
           }
 #pragma unroll
           for (int jj = 0; jj < BATCH; ++jj) {

@@ -329,8 +329,7 @@ void splits_for(int M, int N, int K, int num_sms, int *splits, int *chunk) {
 }
 
 // Buffers of one inner-block update: the panel's V slices (natural and
-// transposed), the split-K partials of W^T = C^T V and the slices of W2.  The
-// look-ahead runs two updates at once, each with its own set.
+// transposed), the split-K partials of W^T = C^T V and the slices of W2.
 struct InnerBufs {
   Slices Vs, Vts, W2s;
   double *Pd = nullptr;
@@ -512,13 +511,6 @@ int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w) {
   w->Pd = ar.take<double>((size_t)QR_MAX_SPLITS * nn * QR_B);
   w->W2s = make_slices(ar.take<__nv_bfloat16>(slice_elems(QR_B, n, S)), QR_B, n, S);
   w->W2s.scale = ar.take<int>(nn);
-  w->Vs2 = make_slices(ar.take<__nv_bfloat16>(slice_elems(m, QR_B, S)), m, QR_B, S);
-  w->Vs2.scale = ar.take<int>(QR_B);
-  w->Vts2 = make_slices(ar.take<__nv_bfloat16>(slice_elems(QR_B, m, S)), QR_B, m, S);
-  w->Vts2.scale = ar.take<int>(mm);
-  w->Pd2 = ar.take<double>((size_t)QR_MAX_SPLITS * nn * QR_B);
-  w->W2s2 = make_slices(ar.take<__nv_bfloat16>(slice_elems(QR_B, n, S)), QR_B, n, S);
-  w->W2s2.scale = ar.take<int>(nn);
   const size_t nout = (size_t)ceil_div(n > 0 ? n : 1, QR_NB);
   w->Tout = ar.take<double>(nout * QR_NB * QR_NB);
   w->Gparts = ar.take<double>((size_t)kGramParts * QR_B * QR_B);
@@ -540,60 +532,21 @@ int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w) {
   return PURL_OK;
 }
 
-// Second stream and two events of the look-ahead, per host thread and device
-// (so concurrent host threads never share them): the lowest priority, so that
-// the panels on the caller's stream are scheduled first.
-struct AuxStream {
-  int device = -1;
-  cudaStream_t s = nullptr;
-  cudaEvent_t go = nullptr, done = nullptr;
-};
-
-int aux_stream(AuxStream **out) {
-  static thread_local AuxStream cache[64];
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PURL_ERR_CUDA;
-  AuxStream &a = cache[dev];
-  if (a.device != dev) {
-    int lo = 0, hi = 0;
-    PURL_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    PURL_CUDA_TRY(cudaStreamCreateWithPriority(&a.s, cudaStreamNonBlocking, lo));
-    PURL_CUDA_TRY(cudaEventCreateWithFlags(&a.go, cudaEventDisableTiming));
-    PURL_CUDA_TRY(cudaEventCreateWithFlags(&a.done, cudaEventDisableTiming));
-    a.device = dev;
-  }
-  *out = &a;
-  return PURL_OK;
-}
-
-// Blocked factorization with look-ahead inside each outer block.  After panel
-// p's reflectors and T are formed, the caller's stream s updates only the next
-// panel's columns and goes on to factor it, while the auxiliary stream a
-// updates the rest of the outer block:
-//   s:  panel p -> V slices -> T_p -> [wait a(p-1)] update panel p+1's columns -> record go_p -> panel p+1 ...
-//   a:  [wait go_p] update columns beyond panel p+1 -> record done_p
-// Column sets are disjoint at any time; a(p-1) (which updated panel p+1's
-// columns with panel p-1's reflectors) completes before s applies panel p's
-// to them.  The two updates use separate buffer sets; the V slices alternate
-// between them by panel parity.  The outer update waits for a.
 int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t s) {
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
   if (n == 0) return PURL_OK;
-  AuxStream *aux = nullptr;
-  PURL_TRY(aux_stream(&aux));
-  const InnerBufs bufs[2] = {{w.Vs, w.Vts, w.W2s, w.Pd}, {w.Vs2, w.Vts2, w.W2s2, w.Pd2}};
+  const InnerBufs b = {w.Vs, w.Vts, w.W2s, w.Pd};
   const int npan = ceil_div(n, QR_B);
   PURL_CUDA_TRY(cudaMemsetAsync(w.base.counters, 0, sizeof(unsigned) * npan, s));
-  bool aux_pending = false;  // work on the auxiliary stream not yet joined into s
   for (int J0 = 0, ob = 0; J0 < n; J0 += QR_NB, ++ob) {
     const int nbw = min(QR_NB, n - J0), rows = m - J0, nc_out = n - J0 - nbw;
-    for (int j0 = J0, k = 0; j0 < J0 + nbw; j0 += QR_B, ++k) {
+    // inner panels, their updates confined to the outer block's columns
+    for (int j0 = J0; j0 < J0 + nbw; j0 += QR_B) {
       const int p = j0 / QR_B, bw = min(QR_B, J0 + nbw - j0), rj = m - j0;
       const int nc_in = J0 + nbw - j0 - bw;
       double *Fp = F + j0 + (size_t)j0 * ldf;
       double *taup = w.base.tau + j0;
-      const InnerBufs &b = bufs[k & 1];
       PURL_TRY(panel_factor(rj, bw, Fp, ldf, taup, w.base.counters + p, w.base, s));
       PURL_TRY(slice_panel(rj, bw, w, b, s));
       // T_k from the FP64 Gram matrix of the rounded V^ (exact to FP64 rounding)
@@ -607,30 +560,8 @@ int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t
       PURL_CUDA_TRY(cudaGetLastError());
       double *Tp = w.base.T + (size_t)p * QR_B * QR_B;
       PURL_TRY(larft_from_gram(bw, 1, w.base.Gp, taup, Tp, s, true));
-      if (nc_in <= 0) continue;
-      // the next panel's columns, on s, after the auxiliary stream's previous update of them
-      if (aux_pending) {
-        PURL_CUDA_TRY(cudaStreamWaitEvent(s, aux->done, 0));
-        aux_pending = false;
-      }
-      const int nxt = min(QR_B, nc_in);
-      PURL_TRY(apply_block_mixed(rj, bw, nxt, Fp + (size_t)bw * ldf, ldf, w.Fs, j0, j0 + bw, w.col_exp, Tp, true, w,
-                                 b, s));
-      const int rest = nc_in - nxt;
-      if (rest > 0) {
-        // the rest of the outer block, on the auxiliary stream
-        PURL_CUDA_TRY(cudaEventRecord(aux->go, s));
-        PURL_CUDA_TRY(cudaStreamWaitEvent(aux->s, aux->go, 0));
-        const InnerBufs ba = {b.Vs, b.Vts, bufs[(k + 1) & 1].W2s, bufs[(k + 1) & 1].Pd};
-        PURL_TRY(apply_block_mixed(rj, bw, rest, Fp + (size_t)(bw + nxt) * ldf, ldf, w.Fs, j0, j0 + bw + nxt,
-                                   w.col_exp, Tp, true, w, ba, aux->s));
-        PURL_CUDA_TRY(cudaEventRecord(aux->done, aux->s));
-        aux_pending = true;
-      }
-    }
-    if (aux_pending) {
-      PURL_CUDA_TRY(cudaStreamWaitEvent(s, aux->done, 0));
-      aux_pending = false;
+      PURL_TRY(apply_block_mixed(rj, bw, nc_in, Fp + (size_t)bw * ldf, ldf, w.Fs, j0, j0 + bw, w.col_exp, Tp, true,
+                                 w, b, s));
     }
     // one aggregated update of everything to the right of the outer block
     double *Tout = w.Tout + (size_t)ob * QR_NB * QR_NB;

@@ -31,10 +31,6 @@ struct QrMixWork {
   Slices Vtls;       // slices of V~ (rows x QR_NB)
   Slices Ts;         // slices of op(T_out) (QR_NB x QR_NB)
   Slices W2o;        // slices of W2 (QR_NB x n)
-  // second set of inner-update buffers for the look-ahead (the update of the
-  // rest of an outer block runs beside the next panel's factorization)
-  Slices Vs2, Vts2, W2s2;
-  double *Pd2 = nullptr;
 };
 
 int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w);
@@ -43,7 +39,6 @@ inline void qr_mixed_use_slices(QrMixWork &w, int S) {
   w.S = S;
   w.Fs.S = S; w.Qs.S = S; w.Vs.S = S; w.Vts.S = S; w.W2s.S = S;
   w.Vos.S = S; w.Vots.S = S; w.Vtls.S = S; w.Ts.S = S; w.W2o.S = S;
-  w.Vs2.S = S; w.Vts2.S = S; w.W2s2.S = S;
 }
 
 // F (m x n, ld ldf) holds M on entry and the packed factor (R above the

@@ -67,7 +67,11 @@ struct UrvWork {
 
 // Slices per operand of the all-exact modes: every product, the power steps
 // included, is an exact-accumulation product of S fixed-point slices.
-constexpr int kFp32Slices = 3;  // 2^-24 of each operand row's scale: FP32's significand
+// FP32 mode: 4 slices carry each operand row to 2^-32 of its scale.  Three
+// (2^-24 of the row's largest entry) leave entries below that maximum with
+// fewer than FP32's 24 bits, which measured ~1e-3 in ||I - Q^T Q||_F at
+// n = 512, above FP32 Householder bounds (~4 n u = 1.2e-4).
+constexpr int kFp32Slices = 4;
 static int exact_slices(int mode) { return mode == PURL_MODE_FP32 ? kFp32Slices : kTcxEmuSlices; }
 
 // FP64 emulation (S = kTcxEmuSlices, every operand row carried to 2^-63 of its

@@ -2,18 +2,19 @@
 points, and the reverse mode run on the tensor cores (purl_urv_backward_ex in
 PURL_MODE_FP64_EMU and PURL_MODE_FP32), against the FP64 oracle.
 
-Bars.  FP32 mode: every product carries each operand row to 2^-24 of its
-scale (u = 2^-24, FP32's unit roundoff), so the factorization is held to
-FP32 Householder bounds of the gamma_{4n} = 4 n u form: relative
-reconstruction and ||I - Q^T Q||_F at most 4 n u, and |R(j,j)| within a
-median 1e-3 of the oracle where sigma_j / sigma_1 >= 1e-2 (its absolute error
-is about sqrt(n) u sigma_1, i.e. ~1e-4 of sigma_j there).  FP64-emulated
-backward: the FP64 path's bars (1e-10 of the largest entry against the
-oracle's reverse mode; 1e-8 in the Frobenius norm against the projection
-formula at 2048).  FP32 backward: the error of the inputs to the R^{-T}
-solves (~sqrt(n) u) is amplified by cond(R): 2e-4 of the largest entry for
-the cond <= 3.3 matrices, 5e-2 in the Frobenius norm at 2048 (Gaussian A,
-cond ~ 1e4: 45 * 6e-8 * 1e4 ~ 3e-2).
+Bars.  FP32 mode: every product carries each operand row to 2^-32 of its
+scale (4 exact slices), so entries down to 2^-8 of their row's maximum keep
+FP32's unit roundoff u = 2^-24; the factorization is held to FP32 Householder
+bounds of the gamma_{4n} = 4 n u form: relative reconstruction and
+||I - Q^T Q||_F at most 4 n u, and |R(j,j)| within a median 1e-3 of the
+oracle where sigma_j / sigma_1 >= 1e-2 (its absolute error is about
+sqrt(n) u sigma_1, i.e. ~1e-4 of sigma_j there).  FP64-emulated backward: the
+FP64 path's bars (1e-10 of the largest entry against the oracle's reverse
+mode; 1e-8 in the Frobenius norm against the projection formula at 2048).
+FP32 backward: the error of the inputs to the R^{-T} solves (~sqrt(n) u) is
+amplified by cond(R): 2e-4 of the largest entry for the cond <= 3.3
+matrices, 5e-2 in the Frobenius norm at 2048 (Gaussian A, cond ~ 1e4:
+45 * 6e-8 * 1e4 ~ 3e-2).
 """
 import numpy as np
 import pytest
