@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--engine", choices=["f64", "tc", "tcx"], default="tcx",
                     help="product: FP64 DFMA engine, plain BF16 slices (tc), or exact slices (tcx)")
     ap.add_argument("--slices", type=int, default=4, help="product: slices per operand")
+    ap.add_argument("--k", type=int, default=0, help="product: reduction length (default n)")
+    ap.add_argument("--update", action="store_true", help="product: C = C - A B instead of C = A B")
     ap.add_argument("--matrix", choices=["haar", "gaussian"], default="haar",
                     help="urv: Haar-factor matrix with sigma_j = 10^(-6(j-1)/(n-1)), or Gaussian entries")
     ap.add_argument("--rank", type=int, default=256, help="rsvd: target rank l")
@@ -1142,19 +1144,24 @@ def run_product(a):
     B.lib()
     dev = torch.device("cuda", torch.cuda.current_device())
     n = a.n
+    k = a.k if a.k > 0 else n
     g = torch.Generator(device=dev)
     g.manual_seed(5)
-    A = torch.randn(n, n, generator=g, device=dev, dtype=torch.float64).t()
-    Bm = torch.randn(n, n, generator=g, device=dev, dtype=torch.float64).t()
+    A = torch.randn(k, n, generator=g, device=dev, dtype=torch.float64).t()
+    Bm = torch.randn(n, k, generator=g, device=dev, dtype=torch.float64).t()
     C = B.empty_colmajor(n, n, dev)
+    C.zero_()
     stream = torch.cuda.current_stream()
     S = a.slices
+    # --update: C <- C - A B (the trailing-update form: FP64 read-modify-write of C)
+    alpha, beta = (-1.0, 1.0) if a.update else (1.0, 0.0)
 
     def step():
         if a.engine == "f64":
-            B.purl_gemm_f64("N", "N", A, Bm, C=C, stream=stream)
+            B.purl_gemm_f64("N", "N", A, Bm, alpha=alpha, beta=beta, C=C, stream=stream)
         else:
-            B.purl_gemm_tc("N", "N", A, Bm, C=C, slices=S, exact=(a.engine == "tcx"), stream=stream)
+            B.purl_gemm_tc("N", "N", A, Bm, alpha=alpha, beta=beta, C=C, slices=S, exact=(a.engine == "tcx"),
+                           stream=stream)
 
     for _ in range(a.warmup):
         step()
@@ -1178,14 +1185,16 @@ def run_product(a):
     if roof is not None:
         attach_traffic(roof)
     err = None
-    if n <= 8192:
+    if n <= 8192 and not a.update:
         ref = A @ Bm
         err = float((C - ref).abs().max() / (A.abs() @ Bm.abs()).max())
-    line = {"metric": f"product C = A B ({a.engine}, slices={S if a.engine != 'f64' else 0})", "value": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+    form = "C = C - A B" if a.update else "C = A B"
+    line = {"metric": f"product {form} ({a.engine}, slices={S if a.engine != 'f64' else 0})",
+            "value": 2.0 * n * n * k / (ms * 1e-3) / 1e12,
             "unit": "TFLOP/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
             "dtype": "f64" if a.engine == "f64" else "bf16 slices",
-            "config": {"workload": f"product m=n=k={n} engine={a.engine} slices={S}",
+            "config": {"workload": f"product m=n={n} k={k} {form} engine={a.engine} slices={S}",
                        "l2": f"operands larger than L2 ({8 * n * n / 2**20:.0f} MiB each)" if 8 * n * n > 129e6
                        else "operands fit in L2"},
             "max_rel_err": err, "clocks": clocks, "roofline": roof,
