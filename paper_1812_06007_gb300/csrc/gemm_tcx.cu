@@ -197,7 +197,10 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(TC_BM, TCX_BN);
+      // The B slices of a stage lie back to back in shared memory (each a
+      // 1024-byte-aligned block of 128-byte rows), and so do the classes in
+      // tensor memory: all products of A slice s with B slices t = 0..T-1
+      // are ONE MMA of N = T * BN columns writing classes s..s+T-1.
       long long kt = 0, ct = 0;  // k-block and chunk counters across work items
       bool stop = false;
       for (long long work = blockIdx.x; work < total && !stop; work += gridDim.x) {
@@ -217,16 +220,16 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
               tc_fence_after();
               const uint32_t sa = smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
               const uint32_t sb = sa + Cfg::A_BYTES;
-              for (int t = 0; t < S - s; ++t) {
-                const uint32_t dcol = tmem + (uint32_t)((b * Cfg::CLASSES + s + t) * TCX_BN);
+              // B slices t < S - s: classes s..S-1
+              const uint32_t dcol = tmem + (uint32_t)((b * Cfg::CLASSES + s) * TCX_BN);
+              const uint32_t idesc = idesc_bf16(TC_BM, (S - s) * TCX_BN);
 #pragma unroll
-                for (int k = 0; k < TC_BK / 16; ++k) {
-                  const uint64_t ad = sw128_desc(sa + k * 32);
-                  const uint64_t bd = sw128_desc(sb + t * Cfg::B_BYTES + k * 32);
-                  // every class d is first reached at s = 0 (t = d): that product
-                  // opens the chunk's accumulator
-                  tc_mma(dcol, ad, bd, idesc, (kin == 0 && s == 0 && k == 0) ? 0u : 1u);
-                }
+              for (int k = 0; k < TC_BK / 16; ++k) {
+                const uint64_t ad = sw128_desc(sa + k * 32);
+                const uint64_t bd = sw128_desc(sb + k * 32);
+                // every class d is first reached at s = 0 (t = d): that product
+                // opens the chunk's accumulator
+                tc_mma(dcol, ad, bd, idesc, (kin == 0 && s == 0 && k == 0) ? 0u : 1u);
               }
               tc_commit(&empty_bar[st]);
             }
@@ -251,18 +254,28 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
           const uint32_t sb = sa + S * Cfg::A_BYTES;
 #pragma unroll
           for (int s = 0; s < S; ++s) {
+            // s + t < S: B slices 0..S-1-s, classes s..S-1, all first reached at
+            // s = 0.  ALL: B slices 0..S-1, classes s..s+S-1; at s >= 1 the last
+            // class s+S-1 is new (its first product overwrites), so that slice
+            // is a second MMA.
+            const int nt = ALL ? (s == 0 ? S : S - 1) : S - s;
+            const uint32_t dcol = tmem + (uint32_t)((b * Cfg::CLASSES + s) * TCX_BN);
+            const uint32_t idesc = idesc_bf16(TC_BM, nt * TCX_BN);
 #pragma unroll
-            for (int t = 0; t < (ALL ? S : S - s); ++t) {
-              const int d = s + t;
-              const uint32_t dcol = tmem + (uint32_t)((b * Cfg::CLASSES + d) * TCX_BN);
-              // class d is first reached at s = max(0, d - (S-1))
-              const bool first = (s == (d > S - 1 ? d - (S - 1) : 0));
+            for (int k = 0; k < TC_BK / 16; ++k) {
+              const uint64_t ad = sw128_desc(sa + s * Cfg::A_BYTES + k * 32);
+              const uint64_t bd = sw128_desc(sb + k * 32);
+              // the first product of a class in a chunk overwrites its accumulator
+              tc_mma(dcol, ad, bd, idesc, (kin == 0 && s == 0 && k == 0) ? 0u : 1u);
+            }
+            if (ALL && s >= 1) {
+              const uint32_t dnew = tmem + (uint32_t)((b * Cfg::CLASSES + s + S - 1) * TCX_BN);
+              constexpr uint32_t idesc1 = idesc_bf16(TC_BM, TCX_BN);
 #pragma unroll
               for (int k = 0; k < TC_BK / 16; ++k) {
                 const uint64_t ad = sw128_desc(sa + s * Cfg::A_BYTES + k * 32);
-                const uint64_t bd = sw128_desc(sb + t * Cfg::B_BYTES + k * 32);
-                // the first product of a class in a chunk overwrites its accumulator
-                tc_mma(dcol, ad, bd, idesc, (kin == 0 && first && k == 0) ? 0u : 1u);
+                const uint64_t bd = sw128_desc(sb + (S - 1) * Cfg::B_BYTES + k * 32);
+                tc_mma(dnew, ad, bd, idesc1, (kin == 0 && k == 0) ? 0u : 1u);
               }
             }
           }

@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "qr.cuh"
 #include "profile.cuh"
+#include "slice_int.cuh"
 
 namespace purl {
 
@@ -42,13 +43,172 @@ constexpr int PNT = 256;  // panel kernel threads
 constexpr int PW = PNT / 32;
 constexpr int kPanelMaxBlocks = 160;  // panel grids have at most this many blocks (>= the SM count)
 
+// ------------------------------------------------------------ panel tail --
+// Shared-memory work arrays of larft_core.
+struct LarftSmem {
+  double Gm[QR_B][QR_B + 1];
+  double Ts[QR_B][QR_B + 1];
+  double tmp[QR_B * QR_B / 2];
+  double tks[QR_B];
+};
+
+// T from the Gram matrix already in L.Gm (bw x bw, symmetric), by the whole
+// block (256 threads).  Ends with a __syncthreads.
+__device__ void larft_core(int bw, LarftSmem &L, const double *tau, double *T, bool tau_from_gram) {
+  constexpr int LF = 8;
+  for (int e = threadIdx.x; e < QR_B * QR_B; e += blockDim.x) L.Ts[e % QR_B][e / QR_B] = 0.0;
+  if (threadIdx.x < bw) {
+    const int k = threadIdx.x;
+    double tk = tau[k];
+    if (tau_from_gram && tk != 0.0) tk = 2.0 / L.Gm[k][k];
+    L.tks[k] = tk;
+  }
+  __syncthreads();
+  // diagonal blocks: thread i owns row i of its block
+  if (threadIdx.x < bw) {
+    const int i = threadIdx.x, a = (i / LF) * LF;
+    for (int k = i; k < a + LF && k < bw; ++k) {
+      if (k == i) {
+        L.Ts[i][k] = L.tks[k];
+      } else {
+        double s0 = 0.0, s1 = 0.0;
+        int l = i;
+        for (; l + 1 < k; l += 2) {
+          s0 = fma(L.Ts[i][l], L.Gm[l][k], s0);
+          s1 = fma(L.Ts[i][l + 1], L.Gm[l + 1][k], s1);
+        }
+        if (l < k) s0 = fma(L.Ts[i][l], L.Gm[l][k], s0);
+        L.Ts[i][k] = -L.tks[k] * (s0 + s1);
+      }
+    }
+  }
+  __syncthreads();
+  for (int h = LF; h < QR_B; h *= 2) {
+    const int outs = (QR_B / (2 * h)) * h * h;
+    for (int e = threadIdx.x; e < outs; e += blockDim.x) {  // tmp = G12 T22
+      const int pr = e / (h * h), i = (e % (h * h)) / h, j = e % h;
+      const int a = pr * 2 * h, b0 = a + h;
+      double s0 = 0.0, s1 = 0.0;
+      for (int l = 0; l <= j; l += 2) {
+        s0 = fma(L.Gm[a + i][b0 + l], L.Ts[b0 + l][b0 + j], s0);
+        if (l + 1 <= j) s1 = fma(L.Gm[a + i][b0 + l + 1], L.Ts[b0 + l + 1][b0 + j], s1);
+      }
+      L.tmp[e] = s0 + s1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < outs; e += blockDim.x) {  // T12 = -T11 tmp
+      const int pr = e / (h * h), i = (e % (h * h)) / h, j = e % h;
+      const int a = pr * 2 * h, b0 = a + h;
+      double s0 = 0.0, s1 = 0.0;
+      for (int l = i; l < h; l += 2) {
+        s0 = fma(L.Ts[a + i][a + l], L.tmp[pr * h * h + l * h + j], s0);
+        if (l + 1 < h) s1 = fma(L.Ts[a + i][a + l + 1], L.tmp[pr * h * h + (l + 1) * h + j], s1);
+      }
+      L.Ts[a + i][b0 + j] = -(s0 + s1);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < QR_B * QR_B; e += blockDim.x) {
+    int i = e % QR_B, j = e / QR_B;
+    T[e] = (i < bw && j < bw) ? L.Ts[i][j] : 0.0;
+  }
+  __syncthreads();
+}
+
+
+// Rounding, slices, Gram matrix and T of a finished panel (see panel_kernel).
+// Ps holds the block's rows of the factored panel; F has been written.
+__device__ void panel_tail(int rows, int bw, int ch, double *Ps, int c, int P, int r0, int nr, const double *tau,
+                           unsigned *counter, DeviceControl *ctrl, const PanelTail &tl) {
+  __shared__ LarftSmem L;
+  __shared__ unsigned char pa[QR_B * (QR_B + 1) / 2], pb[QR_B * (QR_B + 1) / 2];
+  int *es = reinterpret_cast<int *>(Ps + (size_t)ch * QR_B);  // ch row exponents after the panel
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int npairs = bw * (bw + 1) / 2;
+  const double unit = __longlong_as_double((long long)(1023 + tl.vexp - tl.P) << 52);  // 2^(vexp - P)
+  (void)rows;
+  __syncthreads();
+  // (1) V^: 0 above the diagonal, 1 on it, the rounded vector below
+  for (int e = tid; e < nr * bw; e += PNT) {
+    const int i = e % nr, t = e / nr, gi = r0 + i;
+    const double x = Ps[t * ch + i];
+    Ps[t * ch + i] = gi < t ? 0.0 : (gi == t ? 1.0 : (double)fixed_point(x, tl.vexp, tl.P) * unit);
+  }
+  for (int idx = tid; idx < npairs; idx += PNT) {  // upper-triangle pair table (a <= b), column by column
+    int b = 0, rem = idx;
+    while (rem > b) { rem -= b + 1; ++b; }
+    pa[idx] = (unsigned char)rem;
+    pb[idx] = (unsigned char)b;
+  }
+  __syncthreads();
+  // (2) natural slices, exponent vexp per column; (3) row exponents
+  for (int e = tid; e < nr * bw; e += PNT) {
+    const int i = e % nr, t = e / nr;
+    write_fixed_slices(Ps[t * ch + i], tl.vexp, tl.vs.base + (r0 + i) + (long long)t * tl.vs.ld, tl.vs.plane,
+                       tl.vs.S);
+  }
+  if (c == 0 && tid < bw) tl.vs.scale[tid] = tl.vexp;
+  for (int i = tid; i < nr; i += PNT) {
+    unsigned long long mx = 0;
+    for (int t = 0; t < bw; ++t) mx = max(mx, abs_bits(Ps[t * ch + i]));
+    es[i] = exp_above_bits(mx);
+    tl.vts.scale[r0 + i] = es[i];
+  }
+  __syncthreads();
+  // transposed slices, the lanes along the columns
+  for (int e = tid; e < nr * bw; e += PNT) {
+    const int t = e % bw, i = e / bw;
+    write_fixed_slices(Ps[t * ch + i], es[i], tl.vts.base + t + (long long)(r0 + i) * tl.vts.ld, tl.vts.plane,
+                       tl.vts.S);
+  }
+  // (4) this block's part of the Gram matrix: one warp per entry, lanes along rows
+  for (int idx = warp; idx < npairs; idx += PW) {
+    const double *xa = Ps + pa[idx] * ch, *xb = Ps + pb[idx] * ch;
+    double sum = 0.0;
+    for (int i = lane; i < nr; i += 32) sum = fma(xa[i], xb[i], sum);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) __stcg(&tl.gpart[(size_t)c * npairs + idx], sum);
+  }
+  if (!grid_barrier(counter, (unsigned)(bw + 1) * P, ctrl)) return;
+  // (5) distributed sum over the blocks in a fixed order: warp w of block c
+  // takes entry c + P w
+  for (int idx = c + P * warp; idx < npairs; idx += P * PW) {
+    double sum = 0.0;
+    for (int z = lane; z < P; z += 32) sum += __ldcg(&tl.gpart[(size_t)z * npairs + idx]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) __stcg(&tl.G[idx], sum);
+  }
+  if (!grid_barrier(counter, (unsigned)(bw + 2) * P, ctrl)) return;
+  if (c != 0) return;
+  // (6) block 0: T from the Gram matrix (tau_k = 2 / ||v^_k||^2)
+  for (int e = tid; e < QR_B * QR_B; e += PNT) L.Gm[e % QR_B][e / QR_B] = 0.0;
+  __syncthreads();
+  for (int idx = tid; idx < npairs; idx += PNT) {
+    const double g = __ldcg(&tl.G[idx]);
+    L.Gm[pa[idx]][pb[idx]] = g;
+    L.Gm[pb[idx]][pa[idx]] = g;
+  }
+  __syncthreads();
+  larft_core(bw, L, tau, tl.T, true);
+}
+
 // ------------------------------------------------------------ panel -------
 // F points at F(j0, j0); the panel has `rows` rows and `bw` <= QR_B columns.
 // Block c owns panel rows [c*ch, min(rows, (c+1)*ch)).
+//
+// TAIL (the tensor-core QR's panel): after the columns, the blocks also round
+// the Householder vectors to the grid 2^(vexp - P) (V^), write V^'s fixed-point
+// slices (natural, exponent vexp per column; transposed, the exponent of each
+// row's largest entry), form the FP64 Gram matrix V^T V^ (per-block partials,
+// one grid barrier, a distributed sum, another barrier) and block 0 builds T
+// from it with tau_k = 2 / ||v^_k||^2.  Without TAIL the explicit V goes to Vb.
+template <bool TAIL>
 __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, double *F,
                                                     long long ldf, double *Vb, long long ldv,
                                                     double *tau, double *part, double *rowk,
-                                                    unsigned *counter, DeviceControl *ctrl) {
+                                                    unsigned *counter, DeviceControl *ctrl, PanelTail tail) {
   extern __shared__ double Ps[];  // ch x QR_B, column-major (column t at Ps + t*ch)
   __shared__ double s_w[QR_B];
   __shared__ double s_par[4];     // beta, -, tau, 1/v0
@@ -157,8 +317,9 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
     int gi = r0 + i;
     double x = Ps[t * ch + i];
     F[gi + t * ldf] = x;
-    Vb[gi + t * ldv] = (gi < t) ? 0.0 : (gi == t ? 1.0 : x);
+    if constexpr (!TAIL) Vb[gi + t * ldv] = (gi < t) ? 0.0 : (gi == t ? 1.0 : x);
   }
+  if constexpr (TAIL) panel_tail(rows, bw, ch, Ps, c, P, r0, nr, tau, counter, ctrl, tail);
 }
 
 // ------------------------------------------------------------ T factor ----
@@ -176,11 +337,7 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
 // rounded copy of V).
 __global__ void __launch_bounds__(256) larft_kernel(int bw, int splits, const double *Gp,
                                                     const double *tau, double *T, bool tau_from_gram) {
-  constexpr int LF = 8;
-  __shared__ double Gm[QR_B][QR_B + 1];
-  __shared__ double Ts[QR_B][QR_B + 1];
-  __shared__ double tmp[QR_B * QR_B / 2];
-  __shared__ double tks[QR_B];
+  __shared__ LarftSmem L;
   for (int e = threadIdx.x; e < QR_B * QR_B; e += blockDim.x) {
     const int i = e % QR_B, j = e / QR_B;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -195,65 +352,10 @@ __global__ void __launch_bounds__(256) larft_kernel(int bw, int splits, const do
       }
       for (; z < splits; ++z) a0 += Gp[(size_t)z * bw * bw + f];
     }
-    Gm[i][j] = (a0 + a1) + (a2 + a3);
-    Ts[i][j] = 0.0;
+    L.Gm[i][j] = (a0 + a1) + (a2 + a3);
   }
   __syncthreads();
-  if (threadIdx.x < bw) {
-    const int k = threadIdx.x;
-    double tk = tau[k];
-    if (tau_from_gram && tk != 0.0) tk = 2.0 / Gm[k][k];
-    tks[k] = tk;
-  }
-  __syncthreads();
-  // diagonal blocks: thread i owns row i of its block
-  if (threadIdx.x < bw) {
-    const int i = threadIdx.x, a = (i / LF) * LF;
-    for (int k = i; k < a + LF && k < bw; ++k) {
-      if (k == i) {
-        Ts[i][k] = tks[k];
-      } else {
-        double s0 = 0.0, s1 = 0.0;
-        int l = i;
-        for (; l + 1 < k; l += 2) {
-          s0 = fma(Ts[i][l], Gm[l][k], s0);
-          s1 = fma(Ts[i][l + 1], Gm[l + 1][k], s1);
-        }
-        if (l < k) s0 = fma(Ts[i][l], Gm[l][k], s0);
-        Ts[i][k] = -tks[k] * (s0 + s1);
-      }
-    }
-  }
-  __syncthreads();
-  for (int h = LF; h < QR_B; h *= 2) {
-    const int outs = (QR_B / (2 * h)) * h * h;
-    for (int e = threadIdx.x; e < outs; e += blockDim.x) {  // tmp = G12 T22
-      const int pr = e / (h * h), i = (e % (h * h)) / h, j = e % h;
-      const int a = pr * 2 * h, b0 = a + h;
-      double s0 = 0.0, s1 = 0.0;
-      for (int l = 0; l <= j; l += 2) {
-        s0 = fma(Gm[a + i][b0 + l], Ts[b0 + l][b0 + j], s0);
-        if (l + 1 <= j) s1 = fma(Gm[a + i][b0 + l + 1], Ts[b0 + l + 1][b0 + j], s1);
-      }
-      tmp[e] = s0 + s1;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < outs; e += blockDim.x) {  // T12 = -T11 tmp
-      const int pr = e / (h * h), i = (e % (h * h)) / h, j = e % h;
-      const int a = pr * 2 * h, b0 = a + h;
-      double s0 = 0.0, s1 = 0.0;
-      for (int l = i; l < h; l += 2) {
-        s0 = fma(Ts[a + i][a + l], tmp[pr * h * h + l * h + j], s0);
-        if (l + 1 < h) s1 = fma(Ts[a + i][a + l + 1], tmp[pr * h * h + (l + 1) * h + j], s1);
-      }
-      Ts[a + i][b0 + j] = -(s0 + s1);
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < QR_B * QR_B; e += blockDim.x) {
-    int i = e % QR_B, j = e / QR_B;
-    T[e] = (i < bw && j < bw) ? Ts[i][j] : 0.0;
-  }
+  larft_core(bw, L, tau, T, tau_from_gram);
 }
 
 // W2(:, c) = op(T) * sum_z Wp_z(:, c); op(T) = T^T when trans, else T.
@@ -368,25 +470,31 @@ int grid_for(long long total, const DeviceInfo *di) {
 // panel's shared memory changes with every panel (rows shrink), so results
 // are cached per 4 KB step of shared memory, computed for the step's upper
 // end (capacity only falls as shared memory grows); the kernel's dynamic
-// shared-memory limit is only ever raised.
+// shared-memory limit is only ever raised.  Returns 0 when `smem` does not fit
+// beside the kernel's static shared memory.
+template <bool TAIL>
 int panel_capacity(const DeviceInfo *di, size_t smem) {
   static std::mutex mu;
   static std::map<std::pair<int, size_t>, int> cache;
   static std::map<int, size_t> limit;
-  const size_t step = (smem + 4095) / 4096 * 4096;
   std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, panel_kernel<TAIL>) != cudaSuccess) return 0;
+  const size_t room = (size_t)di->max_smem_optin > fa.sharedSizeBytes ? di->max_smem_optin - fa.sharedSizeBytes : 0;
+  if (smem > room) return 0;
+  size_t step = (smem + 4095) / 4096 * 4096;
+  if (step > room) step = room;
   const auto key = std::make_pair(di->device, step);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
-  const size_t want = step < (size_t)di->max_smem_optin ? step : (size_t)di->max_smem_optin;
   size_t &lim = limit[di->device];
-  if (want > 48 * 1024 && want > lim) {
-    if (cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want) != cudaSuccess)
+  if (step > 48 * 1024 - fa.sharedSizeBytes && step > lim) {
+    if (cudaFuncSetAttribute(panel_kernel<TAIL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step) != cudaSuccess)
       return 0;
-    lim = want;
+    lim = step;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, PNT, want) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel<TAIL>, PNT, step) != cudaSuccess) return 0;
   const int cap = per_sm * di->num_sms;
   cache[key] = cap;
   return cap;
@@ -441,15 +549,37 @@ int panel_factor(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *
   int P = panel_blocks(rows, di);
   int ch = ceil_div(rows, P);
   size_t smem = (size_t)ch * QR_B * sizeof(double);
-  if (smem > (size_t)di->max_smem_optin - 4096) return PURL_ERR_UNSUPPORTED;
-  int cap = panel_capacity(di, smem);
+  int cap = panel_capacity<false>(di, smem);
   if (cap < P) return PURL_ERR_UNSUPPORTED;
   int ldv = rows;
   long long ldf_ll = ldf, ldv_ll = ldv;
+  PanelTail none;
   void *args[] = {&rows, &bw, &ch, &Fp, &ldf_ll, &w.Vb, &ldv_ll, &taup, &w.part, &w.rowk, &counter,
-                  (void *)&di->ctrl};
+                  (void *)&di->ctrl, &none};
   LaunchScope ls(KC_PANEL, s, 2.0 * rows * bw * (double)bw, 16.0 * rows * bw, "panel_kernel");
-  PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel, dim3(P), dim3(PNT), args, smem, s));
+  PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel<false>, dim3(P), dim3(PNT), args, smem, s));
+  return PURL_OK;
+}
+
+int panel_factor_tail(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *counter, QrWork &w,
+                      const PanelTail &tail, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  int P = panel_blocks(rows, di);
+  int ch = ceil_div(rows, P);
+  // the panel's rows, then one int per row (the transposed slices' exponents)
+  size_t smem = (size_t)ch * QR_B * sizeof(double) + align_up((size_t)ch * sizeof(int), 16);
+  int cap = panel_capacity<true>(di, smem);
+  if (cap < P) return PURL_ERR_UNSUPPORTED;
+  int ldv = rows;
+  long long ldf_ll = ldf, ldv_ll = ldv;
+  PanelTail tl = tail;
+  void *args[] = {&rows, &bw, &ch, &Fp, &ldf_ll, &w.Vb, &ldv_ll, &taup, &w.part, &w.rowk, &counter,
+                  (void *)&di->ctrl, &tl};
+  // panel flops plus the Gram matrix of the rounded vectors
+  LaunchScope ls(KC_PANEL, s, 2.0 * rows * bw * (double)bw + (double)rows * bw * (bw + 1), 16.0 * rows * bw,
+                 "panel_kernel");
+  PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel<true>, dim3(P), dim3(PNT), args, smem, s));
   return PURL_OK;
 }
 

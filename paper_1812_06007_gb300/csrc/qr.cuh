@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace purl {
 
@@ -20,7 +21,22 @@ struct QrWork {
   unsigned *counters = nullptr;  // one grid-barrier counter per panel
 };
 
+// Outputs of the tensor-core QR's fused panel tail (see panel_kernel): the
+// Householder vectors rounded to the grid 2^(vexp - P), their slices vs
+// (natural) and vts (transposed, one exponent per row), the Gram matrix
+// partials gpart (blocks x bw(bw+1)/2), its sum G (upper triangle, column by
+// column) and the T factor.
+struct PanelTail {
+  int vexp = 1, P = 31;
+  Slices vs, vts;
+  double *gpart = nullptr, *G = nullptr, *T = nullptr;
+};
+
 int qr_plan(Arena &ar, int m, int n, int mode, QrWork *w);
+// One panel of the tensor-core QR with the fused tail (F, tau and the tail's
+// outputs written; w.Vb is not).
+int panel_factor_tail(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *counter, QrWork &w,
+                      const PanelTail &tail, cudaStream_t s);
 int panel_factor(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *counter, QrWork &w,
                  cudaStream_t s);
 int larft_from_gram(int bw, int splits, const double *Gp, const double *taup, double *Tp, cudaStream_t s,

@@ -98,64 +98,53 @@ __global__ void __launch_bounds__(256) split_v_kernel(int rows, int bw, double *
 }
 
 // W2(:, c) = op(T) * sum_z Pd_z(c, :)^T for each trailing column c, then the
-// slices of W2(:, c) with its own exponent.  Block = 32 columns x 8 row groups
-// (thread (cx, ry) owns rows ry, ry+8, ry+16, ry+24 of column cx).
+// slices of W2(:, c) with its own exponent.  Block = 8 columns x 32 rows
+// (thread (cx, l) sums the split-K partials of one entry: the inner updates
+// have few columns, so the work is spread over rows as well).
+constexpr int kTmulCols = 8;
 __global__ void __launch_bounds__(256) reduce_tmul_slices_kernel(int bw, int nc, int splits,
                                                                  const double *__restrict__ Pd,
                                                                  const double *__restrict__ T, bool trans,
                                                                  Slices W2s) {
   __shared__ double Ts[QR_B][QR_B + 1];
-  __shared__ double ws[QR_B][33];
-  __shared__ unsigned long long mxs[8][32];
-  const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
-  const int c = blockIdx.x * 32 + cx;
+  __shared__ double ws[QR_B][kTmulCols + 1];
+  __shared__ unsigned long long mxs[QR_B][kTmulCols];
+  __shared__ int es[kTmulCols];
+  const int cx = threadIdx.x % kTmulCols, l = threadIdx.x / kTmulCols;
+  const int c = blockIdx.x * kTmulCols + cx;
   for (int e = threadIdx.x; e < QR_B * QR_B; e += blockDim.x) {
     const int i = e % QR_B, j = e / QR_B;
     Ts[i][j] = trans ? T[j + i * QR_B] : T[e];  // Ts = op(T)
   }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int l = ry + 8 * q;
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;  // independent loads in flight
-    if (c < nc && l < bw) {
-      const double *pz = Pd + c + (long long)l * nc;
-      const long long st = (long long)nc * bw;
-      int z = 0;
-      for (; z + 3 < splits; z += 4) {
-        v0 += pz[z * st];
-        v1 += pz[(z + 1) * st];
-        v2 += pz[(z + 2) * st];
-        v3 += pz[(z + 3) * st];
-      }
-      for (; z < splits; ++z) v0 += pz[z * st];
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;  // independent loads in flight
+  if (c < nc && l < bw) {
+    const double *pz = Pd + c + (long long)l * nc;
+    const long long st = (long long)nc * bw;
+    int z = 0;
+    for (; z + 3 < splits; z += 4) {
+      v0 += pz[z * st];
+      v1 += pz[(z + 1) * st];
+      v2 += pz[(z + 2) * st];
+      v3 += pz[(z + 3) * st];
     }
-    ws[l][cx] = (v0 + v1) + (v2 + v3);
+    for (; z < splits; ++z) v0 += pz[z * st];
   }
+  ws[l][cx] = (v0 + v1) + (v2 + v3);
   __syncthreads();
-  double w2[4];
-  unsigned long long mx = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int r = ry + 8 * q;
-    double t = 0.0;
+  // row r = l of W2 for column c
+  double t = 0.0;
 #pragma unroll 8
-    for (int l = 0; l < QR_B; ++l) t = fma(Ts[r][l], ws[l][cx], t);
-    w2[q] = t;
-    if (r < bw) mx = max(mx, abs_bits(t));
-  }
-  mxs[ry][cx] = mx;
+  for (int k = 0; k < QR_B; ++k) t = fma(Ts[l][k], ws[k][cx], t);
+  mxs[l][cx] = (l < bw) ? abs_bits(t) : 0ull;
   __syncthreads();
-  unsigned long long m = 0;
-#pragma unroll
-  for (int y = 0; y < 8; ++y) m = max(m, mxs[y][cx]);
-  const int e = exp_above_bits(m);
-  if (c >= nc) return;
-  if (ry == 0) W2s.scale[c] = e;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int r = ry + 8 * q;
-    if (r < bw) write_fixed_slices(w2[q], e, W2s.base + r + (long long)c * W2s.ld, W2s.plane, W2s.S);
+  if (l == 0) {
+    unsigned long long m = 0;
+    for (int y = 0; y < QR_B; ++y) m = max(m, mxs[y][cx]);
+    es[cx] = exp_above_bits(m);
+    if (c < nc) W2s.scale[c] = es[cx];
   }
+  __syncthreads();
+  if (c < nc && l < bw) write_fixed_slices(t, es[cx], W2s.base + l + (long long)c * W2s.ld, W2s.plane, W2s.S);
 }
 
 // Explicit rounded V of an outer block: column t (0 <= t < nbw) of the block
@@ -364,7 +353,7 @@ int apply_block_mixed(int rows, int bw, int nc, double *Cp, int ldc, const Slice
   PURL_TRY(tcx_gemm_view(Cs, r0, c0, b.Vs, 0, 0, nc, bw, rows, w.S, ep, sp, ch, s));
   // W2 = op(T) W, sliced
   { LaunchScope ls(KC_OTHER, s, 2.0 * bw * bw * (double)nc, 8.0 * sp * (double)nc * bw, "reduce_tmul_slices_kernel");
-    reduce_tmul_slices_kernel<<<ceil_div(nc, 32), 256, 0, s>>>(bw, nc, sp, b.Pd, T, trans, b.W2s); }
+    reduce_tmul_slices_kernel<<<ceil_div(nc, kTmulCols), 256, 0, s>>>(bw, nc, sp, b.Pd, T, trans, b.W2s); }
   PURL_CUDA_TRY(cudaGetLastError());
   // C <- C - V W2 (FP64)
   TcEpilogue up;
@@ -547,19 +536,18 @@ int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t
       const int nc_in = J0 + nbw - j0 - bw;
       double *Fp = F + j0 + (size_t)j0 * ldf;
       double *taup = w.base.tau + j0;
-      PURL_TRY(panel_factor(rj, bw, Fp, ldf, taup, w.base.counters + p, w.base, s));
-      PURL_TRY(slice_panel(rj, bw, w, b, s));
-      // T_k from the FP64 Gram matrix of the rounded V^ (exact to FP64 rounding)
-      int gchunk = ceil_div(ceil_div(rj, kGramParts), 64) * 64;
-      if (gchunk < 64) gchunk = 64;
-      const int gs = ceil_div(rj, gchunk);
-      { LaunchScope ls(KC_GEMM_F64, s, 2.0 * rj * bw * (double)bw, 8.0 * rj * bw, "gram_kernel");
-        gram_kernel<<<gs, 256, 0, s>>>(rj, bw, gchunk, w.base.Vb, rj, w.Gparts); }
-      { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "sum_partials_kernel");
-        sum_partials_kernel<<<ceil_div(bw * bw, 64), 64, 0, s>>>(bw * bw, gs, w.Gparts, w.base.Gp); }
-      PURL_CUDA_TRY(cudaGetLastError());
+      // the panel, with its rounded V^, V^'s slices, the FP64 Gram matrix of V^
+      // and T_k (tau_k = 2 / ||v^_k||^2) formed in the same cooperative launch
       double *Tp = w.base.T + (size_t)p * QR_B * QR_B;
-      PURL_TRY(larft_from_gram(bw, 1, w.base.Gp, taup, Tp, s, true));
+      PanelTail tl;
+      tl.vexp = kVExp;
+      tl.P = 7 + 8 * (w.S - 1);
+      tl.vs = b.Vs;
+      tl.vts = b.Vts;
+      tl.gpart = w.Gparts;
+      tl.G = w.base.Gp;
+      tl.T = Tp;
+      PURL_TRY(panel_factor_tail(rj, bw, Fp, ldf, taup, w.base.counters + p, w.base, tl, s));
       PURL_TRY(apply_block_mixed(rj, bw, nc_in, Fp + (size_t)bw * ldf, ldf, w.Fs, j0, j0 + bw, w.col_exp, Tp, true,
                                  w, b, s));
     }
