@@ -43,59 +43,17 @@ void choose_splits(int m, int n, int k, int num_sms, int *splits, int *k_chunk);
 namespace {
 
 constexpr int kChunkAlign = 256;  // exact-accumulation chunk of the tcx engine
-constexpr int kGramParts = 256;   // row chunks of the panel Gram matrix
+constexpr int kGramParts = 256;   // per-block partials of the panel Gram matrix (>= panel blocks)
 
 // Householder vectors with v_k = 1 satisfy |v_i| <= 1 (v = x / (x_0 - beta)
 // and |x_0 - beta| >= ||x||).  Each panel's V is rounded once to the grid
-// 2^-kVGridBits (V^, written back over V), which every slicing below
-// represents exactly: the natural slices use exponent 1 for every column, the
-// transposed ones the exponent of each row's largest entry (any exponent
-// <= 1 carries the grid).  V^ is then one matrix seen identically by V^T C,
-// by the update and by the FP64 Gram matrix that defines T.
+// 2^(kVExp - P), P = 7 + 8(S-1) (V^, inside the panel kernel's fused tail),
+// which every slicing below represents exactly: the natural slices use
+// exponent kVExp for every column, the transposed ones the exponent of each
+// row's largest entry (any exponent <= kVExp carries the grid).  V^ is then
+// one matrix seen identically by V^T C, by the update and by the FP64 Gram
+// matrix that defines T.
 constexpr int kVExp = 1;
-
-// Round each Householder vector to the grid 2^(kVExp - P), P = 7 + 8(S-1)
-// (the last digit of S slices at exponent kVExp), write V^ back over V, and
-// slice V^ naturally (exponent kVExp per column) and transposed (exponent of
-// each row's largest entry, <= kVExp, so the grid is carried exactly).
-__global__ void __launch_bounds__(256) split_v_kernel(int rows, int bw, double *V, long long ldv, Slices vs,
-                                                      Slices vts) {
-  __shared__ double q[32][QR_B + 1];
-  __shared__ int es[32];
-  const int P = 7 + 8 * (vs.S - 1);
-  const double unit = ldexp(1.0, kVExp - P);
-  const int i0 = blockIdx.x * 32;
-  // round and write back, coalesced along rows (thread = (row, column group))
-  for (int e = threadIdx.x; e < 32 * QR_B; e += 256) {
-    const int ii = e & 31, t = e >> 5, i = i0 + ii;
-    double v = 0.0;
-    if (i < rows && t < bw) {
-      v = (double)fixed_point(V[i + t * ldv], kVExp, P) * unit;
-      V[i + t * ldv] = v;
-    }
-    q[ii][t] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    unsigned long long mx = 0;
-    for (int t = 0; t < bw; ++t) mx = max(mx, abs_bits(q[threadIdx.x][t]));
-    es[threadIdx.x] = exp_above_bits(mx);
-    const int i = i0 + threadIdx.x;
-    if (i < rows) vts.scale[i] = es[threadIdx.x];
-    if (i < bw) vs.scale[i] = kVExp;
-  }
-  __syncthreads();
-  // natural slices: coalesced along rows
-  for (int e = threadIdx.x; e < 32 * QR_B; e += 256) {
-    const int ii = e & 31, t = e >> 5, i = i0 + ii;
-    if (i < rows && t < bw) write_fixed_slices(q[ii][t], kVExp, vs.base + i + (long long)t * vs.ld, vs.plane, vs.S);
-  }
-  // transposed slices: coalesced along columns
-  for (int e = threadIdx.x; e < 32 * QR_B; e += 256) {
-    const int t = e & 31, ii = e >> 5, i = i0 + ii;
-    if (i < rows && t < bw) write_fixed_slices(q[ii][t], es[ii], vts.base + t + (long long)i * vts.ld, vts.plane, vts.S);
-  }
-}
 
 // W2(:, c) = op(T) * sum_z Pd_z(c, :)^T for each trailing column c, then the
 // slices of W2(:, c) with its own exponent.  Block = 8 columns x 32 rows
@@ -251,63 +209,62 @@ __global__ void sum_partials_kernel(int count, int splits, const double *__restr
   }
 }
 
-// Y = G(0:kb, kb:kb+bw) T_k  (kb x bw, ld kb).  Thread (i, j) per entry.
-__global__ void tout_y_kernel(int kb, int bw, const double *__restrict__ G, int ldg, const double *__restrict__ Tk,
-                              double *Y) {
-  const int i = blockIdx.x, j = threadIdx.x;
-  if (i >= kb || j >= bw) return;
-  double acc = 0.0;
-  for (int t = 0; t <= j; ++t) acc = fma(G[i + (long long)(kb + t) * ldg], Tk[t + j * QR_B], acc);  // T_k upper
-  Y[i + (long long)j * kb] = acc;
-}
-
-// T_out(0:kb, kb:kb+bw) = -T_out(0:kb, 0:kb) Y, T_out upper triangular.
-__global__ void tout_block_kernel(int kb, int bw, const double *__restrict__ Y, double *Tout, int ldt) {
-  const int i = blockIdx.x, j = threadIdx.x;
-  if (i >= kb || j >= bw) return;
-  double acc = 0.0;
-  for (int l = i; l < kb; ++l) acc = fma(Tout[i + (long long)l * ldt], Y[l + (long long)j * kb], acc);
-  Tout[i + (long long)(kb + j) * ldt] = -acc;
-}
-
-// FP64 Gram matrix partials of the rounded panel V (rows x bw): block z
-// covers rows [z*chunk, (z+1)*chunk) and writes its bw x bw partial at
-// Gp + z*bw*bw (the layout larft_from_gram sums).
-__global__ void __launch_bounds__(256) gram_kernel(int rows, int bw, int chunk, const double *__restrict__ V, int ldv,
-                                                   double *Gp) {
-  __shared__ double Vs[64][QR_B + 1];
-  const int r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  const int e0 = threadIdx.x;  // outputs e0, e0 + 256, e0 + 512, e0 + 768 of the 32 x 32
-  for (int rb = r0; rb < r1; rb += 64) {
-    const int nrow = min(64, r1 - rb);
-    __syncthreads();
-    for (int e = threadIdx.x; e < 64 * QR_B; e += 256) {
-      const int i = e % 64, t = e / 64;
-      Vs[i][t] = (i < nrow && t < bw) ? V[(rb + i) + (long long)t * ldv] : 0.0;
+// T_out of an outer block from its panels' T_k (first at Tk, QR_B x QR_B
+// each) and the exact Gram matrix G of the block's rounded V (nbw x nbw, ld
+// nbw).  The diagonal blocks are the T_k; for every later panel k (columns
+// kb..kb+bw):
+//   Y_k = G(0:kb, kb:kb+bw) T_k,   T_out(0:kb, kb:kb+bw) = -T_out(0:kb, 0:kb) Y_k.
+// One cooperative launch: the diagonal blocks and every Y_k (independent of
+// one another) first, then the column blocks in order with one grid barrier
+// between them.  Tout (ld QR_NB) must be zero on entry; Y holds
+// nk x QR_NB x QR_B doubles; `counter` starts at 0.
+__global__ void __launch_bounds__(256) tout_kernel(int nbw, const double *__restrict__ G,
+                                                   const double *__restrict__ Tk, double *Tout, double *Y,
+                                                   unsigned *counter, DeviceControl *ctrl) {
+  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long GT = (long long)gridDim.x * blockDim.x;
+  const int nk = (nbw + QR_B - 1) / QR_B;
+  // phase 0: diagonal blocks and Y_k, flattened over (k, i, j)
+  for (int k = 0; k < nk; ++k) {
+    const int kb = k * QR_B, bw = min(QR_B, nbw - kb);
+    const double *T = Tk + (size_t)k * QR_B * QR_B;
+    for (long long e = gt; e < (long long)bw * bw; e += GT) {
+      const int i = (int)(e % bw), j = (int)(e / bw);
+      Tout[(kb + i) + (long long)(kb + j) * QR_NB] = T[i + j * QR_B];
     }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = e0 + q * 256, a = e % QR_B, b = e / QR_B;
-      double s = acc[q];
-      for (int i = 0; i < nrow; ++i) s = fma(Vs[i][a], Vs[i][b], s);
-      acc[q] = s;
+    double *Yk = Y + (size_t)k * QR_NB * QR_B;
+    for (long long e = gt; e < (long long)kb * bw; e += GT) {
+      const int i = (int)(e % kb), j = (int)(e / kb);
+      double a0 = 0.0, a1 = 0.0;  // T_k upper triangular: t <= j
+      int t = 0;
+      for (; t + 1 <= j; t += 2) {
+        a0 = fma(G[i + (long long)(kb + t) * nbw], T[t + j * QR_B], a0);
+        a1 = fma(G[i + (long long)(kb + t + 1) * nbw], T[t + 1 + j * QR_B], a1);
+      }
+      if (t <= j) a0 = fma(G[i + (long long)(kb + t) * nbw], T[t + j * QR_B], a0);
+      Yk[i + (long long)j * kb] = a0 + a1;
     }
   }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int e = e0 + q * 256, a = e % QR_B, b = e / QR_B;
-    if (a < bw && b < bw) Gp[(long long)blockIdx.x * bw * bw + a + b * bw] = acc[q];
-  }
-}
-
-// T_out(kb:kb+bw, kb:kb+bw) = T_k (QR_B x QR_B block, ld QR_B) and zero the
-// strictly lower part of that block column.
-__global__ void place_tk_kernel(int nb_ld, int kb, int bw, const double *__restrict__ Tk, double *Tout) {
-  for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) {
-    const int i = e % bw, j = e / bw;
-    Tout[(kb + i) + (long long)(kb + j) * nb_ld] = Tk[i + j * QR_B];
+  unsigned target = gridDim.x;
+  if (!grid_barrier(counter, target, ctrl)) return;
+  for (int k = 1; k < nk; ++k) {
+    const int kb = k * QR_B, bw = min(QR_B, nbw - kb);
+    const double *Yk = Y + (size_t)k * QR_NB * QR_B;
+    for (long long e = gt; e < (long long)kb * bw; e += GT) {
+      const int i = (int)(e % kb), j = (int)(e / kb);
+      double a0 = 0.0, a1 = 0.0;  // T_out(0:kb, 0:kb) upper triangular: l >= i
+      int l = i;
+      for (; l + 1 < kb; l += 2) {
+        a0 = fma(__ldcg(&Tout[i + (long long)l * QR_NB]), Yk[l + (long long)j * kb], a0);
+        a1 = fma(__ldcg(&Tout[i + (long long)(l + 1) * QR_NB]), Yk[l + 1 + (long long)j * kb], a1);
+      }
+      if (l < kb) a0 = fma(__ldcg(&Tout[i + (long long)l * QR_NB]), Yk[l + (long long)j * kb], a0);
+      __stcg(&Tout[i + (long long)(kb + j) * QR_NB], -(a0 + a1));
+    }
+    if (k + 1 < nk) {
+      target += gridDim.x;
+      if (!grid_barrier(counter, target, ctrl)) return;
+    }
   }
 }
 
@@ -323,13 +280,6 @@ struct InnerBufs {
   Slices Vs, Vts, W2s;
   double *Pd = nullptr;
 };
-
-// Slices of the panel's V (natural and transposed) from w.base.Vb (rows x bw).
-int slice_panel(int rows, int bw, QrMixWork &w, const InnerBufs &b, cudaStream_t s) {
-  { LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 4.0 * w.S) * (double)rows * bw, "split_v_kernel");
-    split_v_kernel<<<ceil_div(rows, 32), 256, 0, s>>>(rows, bw, w.base.Vb, rows, b.Vs, b.Vts); }
-  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
-}
 
 // C (rows x nc, FP64 at Cp with ldc) <- (I - V op(T) V^T) C.  The active
 // block is first re-sliced into `Cs` at (r0, c0) with a fresh exponent per
@@ -413,20 +363,16 @@ int outer_prepare(int rows, int nbw, const double *FJ, int ldf, int m, int first
   PURL_CUDA_TRY(cudaGetLastError());
   double *G = w.Tt;  // nbw x nbw, ld nbw
   PURL_CUDA_TRY(cudaMemsetAsync(Tout, 0, sizeof(double) * QR_NB * QR_NB, s));
-  double *X = w.Go;  // scratch after the sum: kb x bw products
-  for (int kb = 0, k = 0; kb < nbw; kb += QR_B, ++k) {
-    const int bw = min(QR_B, nbw - kb);
-    const double *Tk = w.base.T + (size_t)(first_panel + k) * QR_B * QR_B;
-    { LaunchScope ls(KC_OTHER, s, 0.0, 0.0, "place_tk_kernel"); place_tk_kernel<<<1, 256, 0, s>>>(QR_NB, kb, bw, Tk, Tout); }
-    PURL_CUDA_TRY(cudaGetLastError());
-    if (kb == 0) continue;
-    // Y = G(0:kb, kb:kb+bw) T_k;  T_out(0:kb, kb:kb+bw) = -T_out(0:kb, 0:kb) Y
-    { LaunchScope ls(KC_OTHER, s, 2.0 * kb * bw * bw, 0.0, "tout_y_kernel");
-      tout_y_kernel<<<kb, QR_B, 0, s>>>(kb, bw, G, nbw, Tk, X); }
-    { LaunchScope ls(KC_OTHER, s, 1.0 * kb * kb * bw, 0.0, "tout_block_kernel");
-      tout_block_kernel<<<kb, QR_B, 0, s>>>(kb, bw, X, Tout, QR_NB); }
-    PURL_CUDA_TRY(cudaGetLastError());
-  }
+  PURL_CUDA_TRY(cudaMemsetAsync(w.tcount, 0, sizeof(unsigned), s));
+  const double *Tk = w.base.T + (size_t)first_panel * QR_B * QR_B;
+  double *Y = w.Go;  // scratch after the sum: the Y_k
+  int nbw_ = nbw;
+  int grid = di->num_sms;
+  void *args[] = {&nbw_, &G, &Tk, &Tout, &Y, &w.tcount, (void *)&di->ctrl};
+  double fl = 0.0;
+  for (int kb = QR_B; kb < nbw; kb += QR_B) fl += 2.0 * kb * QR_B * QR_B / 2 + 1.0 * kb * kb * QR_B;
+  LaunchScope ls(KC_OTHER, s, fl, 8.0 * nbw * (double)nbw, "tout_kernel");
+  PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)tout_kernel, dim3(grid), dim3(256), args, 0, s));
   return PURL_OK;
 }
 
@@ -518,6 +464,7 @@ int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w) {
   w->Ts.scale = ar.take<int>(QR_NB);
   w->W2o = make_slices(ar.take<__nv_bfloat16>(slice_elems(QR_NB, n, S)), QR_NB, n, S);
   w->W2o.scale = ar.take<int>(nn);
+  w->tcount = ar.take<unsigned>(1);
   return PURL_OK;
 }
 

@@ -31,6 +31,7 @@ struct QrMixWork {
   Slices Vtls;       // slices of V~ (rows x QR_NB)
   Slices Ts;         // slices of op(T_out) (QR_NB x QR_NB)
   Slices W2o;        // slices of W2 (QR_NB x n)
+  unsigned *tcount = nullptr;  // grid-barrier counter of the T_out assembly
 };
 
 int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w);
