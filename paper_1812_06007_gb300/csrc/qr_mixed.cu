@@ -235,14 +235,22 @@ __global__ void __launch_bounds__(256) tout_kernel(int nbw, const double *__rest
     double *Yk = Y + (size_t)k * QR_NB * QR_B;
     for (long long e = gt; e < (long long)kb * bw; e += GT) {
       const int i = (int)(e % kb), j = (int)(e / kb);
-      double a0 = 0.0, a1 = 0.0;  // T_k upper triangular: t <= j
+      const double *gr = G + i + (long long)kb * nbw;
+      const double *tc = T + j * QR_B;
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};  // T_k upper triangular: t <= j
       int t = 0;
-      for (; t + 1 <= j; t += 2) {
-        a0 = fma(G[i + (long long)(kb + t) * nbw], T[t + j * QR_B], a0);
-        a1 = fma(G[i + (long long)(kb + t + 1) * nbw], T[t + 1 + j * QR_B], a1);
+      for (; t + 7 <= j; t += 8) {
+        double gv[8], tv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          gv[u] = gr[(long long)(t + u) * nbw];
+          tv[u] = tc[t + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u & 3] = fma(gv[u], tv[u], acc[u & 3]);
       }
-      if (t <= j) a0 = fma(G[i + (long long)(kb + t) * nbw], T[t + j * QR_B], a0);
-      Yk[i + (long long)j * kb] = a0 + a1;
+      for (; t <= j; ++t) acc[0] = fma(gr[(long long)t * nbw], tc[t], acc[0]);
+      Yk[i + (long long)j * kb] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
   }
   unsigned target = gridDim.x;
@@ -252,14 +260,24 @@ __global__ void __launch_bounds__(256) tout_kernel(int nbw, const double *__rest
     const double *Yk = Y + (size_t)k * QR_NB * QR_B;
     for (long long e = gt; e < (long long)kb * bw; e += GT) {
       const int i = (int)(e % kb), j = (int)(e / kb);
-      double a0 = 0.0, a1 = 0.0;  // T_out(0:kb, 0:kb) upper triangular: l >= i
+      // T_out(0:kb, 0:kb) upper triangular: l >= i.  Loads go out 8 at a time
+      // (they come from L2); no line of a column is read before it is final.
+      const double *tr = Tout + i;
+      const double *yc = Yk + (long long)j * kb;
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
       int l = i;
-      for (; l + 1 < kb; l += 2) {
-        a0 = fma(__ldcg(&Tout[i + (long long)l * QR_NB]), Yk[l + (long long)j * kb], a0);
-        a1 = fma(__ldcg(&Tout[i + (long long)(l + 1) * QR_NB]), Yk[l + 1 + (long long)j * kb], a1);
+      for (; l + 7 < kb; l += 8) {
+        double tv[8], yv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          tv[u] = __ldcg(&tr[(long long)(l + u) * QR_NB]);
+          yv[u] = yc[l + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u & 3] = fma(tv[u], yv[u], acc[u & 3]);
       }
-      if (l < kb) a0 = fma(__ldcg(&Tout[i + (long long)l * QR_NB]), Yk[l + (long long)j * kb], a0);
-      __stcg(&Tout[i + (long long)(kb + j) * QR_NB], -(a0 + a1));
+      for (; l < kb; ++l) acc[0] = fma(__ldcg(&tr[(long long)l * QR_NB]), yc[l], acc[0]);
+      __stcg(&Tout[i + (long long)(kb + j) * QR_NB], -((acc[0] + acc[1]) + (acc[2] + acc[3])));
     }
     if (k + 1 < nk) {
       target += gridDim.x;
