@@ -398,31 +398,22 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
             const int col = n0 + cbase + j;
             if (col < N) {
               const int k = ea + scB[vb.c0 + col] - 14;
-              // narrow: hi + lo rounded once by integer operations (one FP64
-              // add fewer per output on a pipe of 2 per clock per SM); wide:
-              // two exact partial sums 2^32 apart, joined by FP64 adds
               double dh, dl;
               if constexpr (Cfg::WIDE) {
                 dh = int64_scaled_to_double(accH[j], k + 32 - 8 * (S - 1));
                 dl = int64_scaled_to_double(accL[j], k - 8 * (S - 1));
               } else {
-                dh = hilo_to_double(hi[j], lo[j], k);
-                dl = 0.0;
+                dh = scaled_float_to_double(hi[j], k);
+                dl = scaled_float_to_double(lo[j], k);
               }
               if (ep.mode == 0) {
                 double *p = ep.C + row + (long long)col * ep.ldc;
                 double x;
-                if constexpr (Cfg::WIDE) {
-                  if (subtract) x = (cv[jj] - dh) - dl;
-                  else if (plain) x = dh + dl;
-                  else {
-                    const double val = dh + dl;
-                    x = (ep.beta == 0.0) ? ep.alpha * val : fma(ep.alpha, val, ep.beta * cv[jj]);
-                  }
-                } else {
-                  if (subtract) x = cv[jj] - dh;
-                  else if (plain) x = dh;
-                  else x = (ep.beta == 0.0) ? ep.alpha * dh : fma(ep.alpha, dh, ep.beta * cv[jj]);
+                if (subtract) x = (cv[jj] - dh) - dl;
+                else if (plain) x = dh + dl;
+                else {
+                  const double val = dh + dl;
+                  x = (ep.beta == 0.0) ? ep.alpha * val : fma(ep.alpha, val, ep.beta * cv[jj]);
                 }
                 *p = x;
                 if (ep.out.base) {
@@ -431,7 +422,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
                   else write_slices(x, o, ep.out.plane, ep.out.S);
                 }
               } else {
-                ep.Pd[(long long)z * M * N + row + (long long)col * M] = Cfg::WIDE ? dh + dl : dh;
+                ep.Pd[(long long)z * M * N + row + (long long)col * M] = dh + dl;
               }
             }
           }

@@ -90,17 +90,6 @@ __device__ __forceinline__ double scaled_float_to_double(float f, int k) {
   return __longlong_as_double((long long)(sign | (e11 << 52) | m));
 }
 
-// Signed integer mantissa and exponent of a finite FP32 value: f = m 2^e with
-// |m| < 2^24; zero and subnormals give m = 0.
-__device__ __forceinline__ void float_parts(float f, long long &m, int &e) {
-  const unsigned b = __float_as_uint(f);
-  const int e8 = (int)((b >> 23) & 0xFFu);
-  if (e8 == 0) { m = 0; e = 0; return; }
-  const long long a = (long long)((b & 0x7FFFFFu) | 0x800000u);
-  m = (b >> 31) ? -a : a;
-  e = e8 - 150;
-}
-
 // The FP64 value nearest to x * 2^k (ties away from zero) for |x| < 2^62,
 // assembled with integer operations only; zero for x == 0 and for results
 // below the normal FP64 range.
@@ -123,28 +112,6 @@ __device__ __forceinline__ double int64_scaled_to_double(long long x, int k) {
   const int E = msb + k + 1023;
   if (E <= 0) return 0.0;
   return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
-}
-
-// The FP64 value nearest to (hi + lo) 2^k for finite FP32 hi, lo, from
-// integer operations: both become signed integers on the unit of the one with
-// the smaller exponent, their sum is exact in 64 bits and rounded once (ties
-// away from zero).  (A two-sum pair usually has |lo| <= ulp(hi), but after
-// cancellation lo may be the larger.)  When one part lies more than 2^38 below
-// the other's unit it is dropped: below 2^-37 of the result.
-__device__ __forceinline__ double hilo_to_double(float hi, float lo, int k) {
-  long long mh, ml;
-  int eh, el;
-  float_parts(hi, mh, eh);
-  float_parts(lo, ml, el);
-  if (mh == 0) return int64_scaled_to_double(ml, el + k);
-  if (ml == 0) return int64_scaled_to_double(mh, eh + k);
-  const int d = eh - el;
-  if (d >= 0) {
-    if (d > 38) return int64_scaled_to_double(mh, eh + k);
-    return int64_scaled_to_double(mh * (1LL << d) + ml, el + k);
-  }
-  if (-d > 38) return int64_scaled_to_double(ml, el + k);
-  return int64_scaled_to_double(ml * (1LL << -d) + mh, eh + k);
 }
 
 }  // namespace purl
