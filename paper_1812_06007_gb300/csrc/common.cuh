@@ -47,6 +47,11 @@ const DeviceInfo *device_info();
 int noalloc_take_status(int *status);
 int noalloc_control(DeviceControl **ctrl);
 
+// Zero `bytes` (a multiple of 4) of device memory with a kernel rather than
+// cudaMemsetAsync, so that the many small clears of a factorization leave the
+// copy engines to the caller's host transfers.
+int zero_async(void *p, size_t bytes, cudaStream_t s);
+
 // Non-finite input: finite_check zeroes *flag (device int), scans the m x n
 // matrix and, if any entry is NaN or infinite, sets *flag and records
 // PURL_ERR_NONFINITE in the device status word; finite_poison overwrites the

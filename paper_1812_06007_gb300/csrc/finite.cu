@@ -47,12 +47,30 @@ __global__ void finite_poison_kernel(const int *flag, int m, int n, double *X, l
     X[(e % m) + (e / m) * ldx] = nan;
 }
 
+__global__ void zero_words_kernel(unsigned *p, long long words) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < words;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = 0u;
+}
+
 }  // namespace
+
+int zero_async(void *p, size_t bytes, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  const long long words = (long long)(bytes / 4);
+  if (words == 0) return PURL_OK;
+  long long blocks = (words + 255) / 256;
+  if (blocks > (long long)di->num_sms * 4) blocks = (long long)di->num_sms * 4;
+  LaunchScope ls(KC_OTHER, s, 0.0, (double)bytes, "zero_words_kernel");
+  zero_words_kernel<<<(int)blocks, 256, 0, s>>>(static_cast<unsigned *>(p), words);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
+}
 
 int finite_check(int m, int n, const double *A, long long lda, int *flag, cudaStream_t s) {
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
-  PURL_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  PURL_TRY(zero_async(flag, sizeof(int), s));
   const long long total = (long long)m * n;
   if (total == 0) return PURL_OK;
   const long long warps = (long long)((m + 31) / 32) * n;

@@ -377,7 +377,7 @@ int split_scaled(int R, int Cc, const double *X, long long ldx, Slices dst, int 
   const long long total = (long long)R * Cc;
   if (total == 0) return PURL_OK;
   if (dst.S != 1) return PURL_ERR_UNSUPPORTED;
-  PURL_CUDA_TRY(cudaMemsetAsync(e_ws, 0, sizeof(int), s));
+  PURL_TRY(zero_async(e_ws, sizeof(int), s));
   long long g = (total + 255) / 256;
   if (g > (long long)di->num_sms * 8) g = (long long)di->num_sms * 8;
   {

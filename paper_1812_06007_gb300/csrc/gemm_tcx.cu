@@ -442,6 +442,11 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
 
 // One block per column: exponent of the column maximum (or the given one),
 // then the fixed-point slices of the column (integer arithmetic only).
+// One block per column: exponent of the column maximum (or the given one),
+// then the fixed-point slices of the column (integer arithmetic only).  When
+// the column and the slice planes are aligned, a thread takes two rows at a
+// time: one 16-byte load, one 4-byte store per slice for the pair.
+template <int S>
 __global__ void __launch_bounds__(256) split_exact_kernel(int R, int Cc, const double *__restrict__ X, long long ldx,
                                                           Slices dst, const int *__restrict__ scale_from) {
   __shared__ unsigned long long red[8];
@@ -466,8 +471,30 @@ __global__ void __launch_bounds__(256) split_exact_kernel(int R, int Cc, const d
     __syncthreads();
     const int e = s_e;
     if (threadIdx.x == 0 && dst.scale) dst.scale[c] = e;
-    for (int r = threadIdx.x; r < R; r += 256)
-      write_fixed_slices(col[r], e, dst.base + r + (long long)c * dst.ld, dst.plane, dst.S);
+    unsigned short *out = reinterpret_cast<unsigned short *>(dst.base) + (long long)c * dst.ld;
+    const bool pairs = ((reinterpret_cast<uintptr_t>(col) & 15) == 0) &&
+                       ((reinterpret_cast<uintptr_t>(out) & 3) == 0) && ((dst.plane & 1) == 0);
+    int r_done = 0;
+    if (pairs) {
+      const int R2 = R >> 1;
+      const double2 *col2 = reinterpret_cast<const double2 *>(col);
+      for (int r2 = threadIdx.x; r2 < R2; r2 += 256) {
+        const double2 v = col2[r2];
+        unsigned short d0[S], d1[S];
+        fixed_digits<S>(v.x, e, d0);
+        fixed_digits<S>(v.y, e, d1);
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl)
+          reinterpret_cast<unsigned *>(out + sl * dst.plane)[r2] = (unsigned)d0[sl] | ((unsigned)d1[sl] << 16);
+      }
+      r_done = R2 << 1;
+    }
+    for (int r = r_done + threadIdx.x; r < R; r += 256) {
+      unsigned short d[S];
+      fixed_digits<S>(col[r], e, d);
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl) out[sl * dst.plane + r] = d[sl];
+    }
     __syncthreads();
   }
 }
@@ -537,7 +564,17 @@ int split_exact(int R, int Cc, const double *X, long long ldx, Slices dst, const
   const int cap = R > 4096 ? di->num_sms * 4 : di->num_sms * 32;
   int grid = Cc < cap ? Cc : cap;
   LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * dst.S) * (double)R * Cc, "split_exact_kernel");
-  split_exact_kernel<<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from);
+  switch (dst.S) {
+    case 1: split_exact_kernel<1><<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from); break;
+    case 2: split_exact_kernel<2><<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from); break;
+    case 3: split_exact_kernel<3><<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from); break;
+    case 4: split_exact_kernel<4><<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from); break;
+    case 5: split_exact_kernel<5><<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from); break;
+    case 6: split_exact_kernel<6><<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from); break;
+    case 7: split_exact_kernel<7><<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from); break;
+    case 8: split_exact_kernel<8><<<grid, 256, 0, s>>>(R, Cc, X, ldx, dst, scale_from); break;
+    default: return PURL_ERR_UNSUPPORTED;
+  }
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 

@@ -610,7 +610,7 @@ int qr_factor_f64(int m, int n, double *F, int ldf, QrWork &w, cudaStream_t s) {
   if (!di) return PURL_ERR_CUDA;
   if (n == 0) return PURL_OK;
   int npan = ceil_div(n, QR_B);
-  PURL_CUDA_TRY(cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * npan, s));
+  PURL_TRY(zero_async(w.counters, sizeof(unsigned) * npan, s));
   for (int p = 0; p < npan; ++p) {
     int j0 = p * QR_B;
     int bw = min(QR_B, n - j0);

@@ -216,7 +216,8 @@ __global__ void sum_partials_kernel(int count, int splits, const double *__restr
 //   Y_k = G(0:kb, kb:kb+bw) T_k,   T_out(0:kb, kb:kb+bw) = -T_out(0:kb, 0:kb) Y_k.
 // One cooperative launch: the diagonal blocks and every Y_k (independent of
 // one another) first, then the column blocks in order with one grid barrier
-// between them.  Tout (ld QR_NB) must be zero on entry; Y holds
+// between them.  Tout (ld QR_NB) is written whole (zeros outside the upper
+// block triangle); Y holds
 // nk x QR_NB x QR_B doubles; `counter` starts at 0.
 __global__ void __launch_bounds__(256) tout_kernel(int nbw, const double *__restrict__ G,
                                                    const double *__restrict__ Tk, double *Tout, double *Y,
@@ -224,7 +225,11 @@ __global__ void __launch_bounds__(256) tout_kernel(int nbw, const double *__rest
   const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long GT = (long long)gridDim.x * blockDim.x;
   const int nk = (nbw + QR_B - 1) / QR_B;
-  // phase 0: diagonal blocks and Y_k, flattened over (k, i, j)
+  // phase 0: zeros below the diagonal blocks, the diagonal blocks and Y_k
+  for (long long e = gt; e < (long long)QR_NB * QR_NB; e += GT) {
+    const int i = (int)(e % QR_NB), j = (int)(e / QR_NB);
+    if ((i / QR_B) > (j / QR_B) || i >= nbw || j >= nbw) Tout[e] = 0.0;
+  }
   for (int k = 0; k < nk; ++k) {
     const int kb = k * QR_B, bw = min(QR_B, nbw - kb);
     const double *T = Tk + (size_t)k * QR_B * QR_B;
@@ -380,8 +385,7 @@ int outer_prepare(int rows, int nbw, const double *FJ, int ldf, int m, int first
     sum_partials_kernel<<<launch_grid((long long)nbw * nbw, 256), 256, 0, s>>>(nbw * nbw, gs, w.Go, w.Tt); }
   PURL_CUDA_TRY(cudaGetLastError());
   double *G = w.Tt;  // nbw x nbw, ld nbw
-  PURL_CUDA_TRY(cudaMemsetAsync(Tout, 0, sizeof(double) * QR_NB * QR_NB, s));
-  PURL_CUDA_TRY(cudaMemsetAsync(w.tcount, 0, sizeof(unsigned), s));
+  PURL_TRY(zero_async(w.tcount, sizeof(unsigned), s));
   const double *Tk = w.base.T + (size_t)first_panel * QR_B * QR_B;
   double *Y = w.Go;  // scratch after the sum: the Y_k
   int nbw_ = nbw;
@@ -492,7 +496,7 @@ int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t
   if (n == 0) return PURL_OK;
   const InnerBufs b = {w.Vs, w.Vts, w.W2s, w.Pd};
   const int npan = ceil_div(n, QR_B);
-  PURL_CUDA_TRY(cudaMemsetAsync(w.base.counters, 0, sizeof(unsigned) * npan, s));
+  PURL_TRY(zero_async(w.base.counters, sizeof(unsigned) * npan, s));
   for (int J0 = 0, ob = 0; J0 < n; J0 += QR_NB, ++ob) {
     const int nbw = min(QR_NB, n - J0), rows = m - J0, nc_out = n - J0 - nbw;
     // inner panels, their updates confined to the outer block's columns

@@ -76,6 +76,20 @@ __device__ __forceinline__ void write_fixed_slices(double x, int e, __nv_bfloat1
   }
 }
 
+// The same digits as write_fixed_slices for a compile-time S, returned as BF16
+// bit patterns (d[0] the top digit).
+template <int S>
+__device__ __forceinline__ void fixed_digits(double x, int e, unsigned short (&d)[S]) {
+  const long long n = fixed_point(x, e, 7 + 8 * (S - 1));
+  const unsigned long long M = (unsigned long long)n + (0x0080808080808080ULL >> (8 * (8 - S)));
+  int t = (int)((M >> (8 * (S - 1))) & 255u);
+  t = t >= 128 ? t - 256 : t;
+  if (t == -128 && n > 0) t = 128;
+  d[0] = bf16_bits_small(t);
+#pragma unroll
+  for (int s = 1; s < S; ++s) d[s] = bf16_bits_small((int)((M >> (8 * (S - 1 - s))) & 255u) - 128);
+}
+
 // The FP64 value of f * 2^k for a finite FP32 f, assembled from the bits of f
 // with integer operations (no FP64-pipe instruction).  Zero and FP32
 // subnormals (|f| < 2^-126, far below every value these kernels produce)
