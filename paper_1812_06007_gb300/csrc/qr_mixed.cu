@@ -105,47 +105,54 @@ __global__ void __launch_bounds__(256) reduce_tmul_slices_kernel(int bw, int nc,
   if (c < nc && l < bw) write_fixed_slices(t, es[cx], W2s.base + l + (long long)c * W2s.ld, W2s.plane, W2s.S);
 }
 
-// Explicit rounded V of an outer block: column t (0 <= t < nbw) of the block
-// is the Householder vector of global column J0 + t, i.e. 0 above row t, 1 at
-// row t, the rounded stored entries below (rows counted from J0).
-__global__ void extract_round_v_kernel(int rows, int nbw, const double *__restrict__ F, long long ldf, double *Vo,
-                                       long long ldv, int P) {
-  const double unit = ldexp(1.0, kVExp - P);
-  const long long total = (long long)rows * nbw;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % rows), t = (int)(e / rows);
-    double v = 0.0;
-    if (i == t) v = 1.0;
-    else if (i > t) v = (double)fixed_point(F[i + (long long)t * ldf], kVExp, P) * unit;
-    Vo[i + (long long)t * ldv] = v;
-  }
-}
-
-// Slices of X^T (nbw x rows) with one exponent per row of X (rows x nbw):
-// row_exp_kernel takes the exponent of each row's maximum (coalesced across
-// rows), split_rows_t_kernel writes the digits through a 32 x 32 shared tile
-// so both the reads of X and the writes of X^T's slices are coalesced.
-__global__ void row_exp_kernel(int rows, int nbw, const double *__restrict__ X, long long ldx, int *e_out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
-    unsigned long long mx = 0;
-    for (int t = 0; t < nbw; ++t) mx = max(mx, abs_bits(X[i + (long long)t * ldx]));
-    e_out[i] = exp_above_bits(mx);
-  }
-}
-
-__global__ void split_rows_t_kernel(int rows, int nbw, const double *__restrict__ X, long long ldx, Slices dst) {
+// Explicit rounded V of an outer block and its transposed slices, one block
+// per 32 rows.  Column t (0 <= t < nbw) of the block is the Householder
+// vector of global column J0 + t: 0 above row t, 1 at row t, the stored
+// entries below rounded to the grid 2^(kVExp - P) (rows counted from J0).
+// Pass 1 writes Vo (lanes along rows) and takes each row's largest entry;
+// pass 2 re-reads the block's rows of Vo (from L2) through a 32 x 32 shared
+// tile and writes the slices of Vo^T with one exponent per row of Vo, lanes
+// along the columns.
+__global__ void __launch_bounds__(256) outer_v_kernel(int rows, int nbw, const double *__restrict__ F, long long ldf,
+                                                      double *Vo, long long ldv, int P, Slices vts) {
+  __shared__ unsigned long long mx_s[8][32];
+  __shared__ int es[32];
   __shared__ double tile[32][33];
-  const int i0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const int i = i0 + threadIdx.x, t = t0 + j;
-    tile[j][threadIdx.x] = (i < rows && t < nbw) ? X[i + (long long)t * ldx] : 0.0;
+  const double unit = ldexp(1.0, kVExp - P);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r0 = blockIdx.x * 32, i = r0 + lane;
+  unsigned long long mx = 0;
+  for (int t = warp; t < nbw; t += 8) {
+    double v = 0.0;
+    if (i < rows) {
+      if (i == t) v = 1.0;
+      else if (i > t) v = (double)fixed_point(F[i + (long long)t * ldf], kVExp, P) * unit;
+      Vo[i + (long long)t * ldv] = v;
+    }
+    mx = max(mx, abs_bits(v));
+  }
+  mx_s[warp][lane] = mx;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long m = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m = max(m, mx_s[w][lane]);
+    es[lane] = exp_above_bits(m);
+    if (i < rows) vts.scale[i] = es[lane];
   }
   __syncthreads();
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const int t = t0 + threadIdx.x, i = i0 + j;  // dst(t, i) = X(i, t)
-    if (i < rows && t < nbw)
-      write_fixed_slices(tile[threadIdx.x][j], dst.scale[i], dst.base + t + (long long)i * dst.ld, dst.plane, dst.S);
+  for (int t0 = 0; t0 < nbw; t0 += 32) {
+    for (int j = warp; j < 32; j += 8) {  // tile[j][lane] = Vo(r0 + lane, t0 + j)
+      const int t = t0 + j;
+      tile[j][lane] = (i < rows && t < nbw) ? Vo[i + (long long)t * ldv] : 0.0;
+    }
+    __syncthreads();
+    for (int j = warp; j < 32; j += 8) {  // row r0 + j of Vo, lanes along its columns
+      const int t = t0 + lane, ii = r0 + j;
+      if (ii < rows && t < nbw)
+        write_fixed_slices(tile[lane][j], es[j], vts.base + t + (long long)ii * vts.ld, vts.plane, vts.S);
+    }
+    __syncthreads();
   }
 }
 
@@ -211,83 +218,86 @@ __global__ void sum_partials_kernel(int count, int splits, const double *__restr
 
 // T_out of an outer block from its panels' T_k (first at Tk, QR_B x QR_B
 // each) and the exact Gram matrix G of the block's rounded V (nbw x nbw, ld
-// nbw).  The diagonal blocks are the T_k; for every later panel k (columns
-// kb..kb+bw):
-//   Y_k = G(0:kb, kb:kb+bw) T_k,   T_out(0:kb, kb:kb+bw) = -T_out(0:kb, 0:kb) Y_k.
-// One cooperative launch: the diagonal blocks and every Y_k (independent of
-// one another) first, then the column blocks in order with one grid barrier
-// between them.  Tout (ld QR_NB) is written whole (zeros outside the upper
-// block triangle); Y holds
-// nk x QR_NB x QR_B doubles; `counter` starts at 0.
+// nbw), by recursive doubling: the diagonal 32-blocks are the T_k, and level
+// L = 1, 2, ... merges adjacent blocks of h = 32 * 2^(L-1) columns,
+//   T(a, b) = -T(a, a) (G(a, b) T(b, b)),
+// all merges of a level at once: X = G(a, b) T(b, b), grid barrier,
+// T(a, b) = -T(a, a) X, grid barrier.  (The compact-WY T of two reflector
+// sets with T1 and T2 and V1^T V2 = G12.)  One cooperative launch; Tout (ld
+// QR_NB) is written whole (zeros outside the upper block triangle); X holds
+// QR_NB x QR_NB / 2 doubles; `counter` starts at 0.
+__device__ __forceinline__ void tout_barrier(unsigned *counter, unsigned &target, DeviceControl *ctrl, bool &ok) {
+  target += gridDim.x;
+  if (ok) ok = grid_barrier(counter, target, ctrl);
+}
+
 __global__ void __launch_bounds__(256) tout_kernel(int nbw, const double *__restrict__ G,
-                                                   const double *__restrict__ Tk, double *Tout, double *Y,
+                                                   const double *__restrict__ Tk, double *Tout, double *X,
                                                    unsigned *counter, DeviceControl *ctrl) {
   const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long GT = (long long)gridDim.x * blockDim.x;
   const int nk = (nbw + QR_B - 1) / QR_B;
-  // phase 0: zeros below the diagonal blocks, the diagonal blocks and Y_k
+  // level 0: zeros outside the diagonal blocks' upper block triangle, the diagonal blocks
   for (long long e = gt; e < (long long)QR_NB * QR_NB; e += GT) {
     const int i = (int)(e % QR_NB), j = (int)(e / QR_NB);
-    if ((i / QR_B) > (j / QR_B) || i >= nbw || j >= nbw) Tout[e] = 0.0;
+    const int bi = i / QR_B, bj = j / QR_B;
+    double v = 0.0;
+    if (i < nbw && j < nbw && bi == bj) v = Tk[(size_t)bi * QR_B * QR_B + (i % QR_B) + (j % QR_B) * QR_B];
+    if (!(i < nbw && j < nbw && bi < bj)) Tout[e] = v;  // upper blocks come from the merges
   }
-  for (int k = 0; k < nk; ++k) {
-    const int kb = k * QR_B, bw = min(QR_B, nbw - kb);
-    const double *T = Tk + (size_t)k * QR_B * QR_B;
-    for (long long e = gt; e < (long long)bw * bw; e += GT) {
-      const int i = (int)(e % bw), j = (int)(e / bw);
-      Tout[(kb + i) + (long long)(kb + j) * QR_NB] = T[i + j * QR_B];
-    }
-    double *Yk = Y + (size_t)k * QR_NB * QR_B;
-    for (long long e = gt; e < (long long)kb * bw; e += GT) {
-      const int i = (int)(e % kb), j = (int)(e / kb);
-      const double *gr = G + i + (long long)kb * nbw;
-      const double *tc = T + j * QR_B;
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};  // T_k upper triangular: t <= j
+  unsigned target = 0;
+  bool ok = true;
+  tout_barrier(counter, target, ctrl, ok);
+  for (int h = QR_B; h < nk * QR_B && ok; h *= 2) {
+    // merges p: a = [2p h, 2p h + h), b = [2p h + h, min(2p h + 2h, nbw)); X_p at X + p h h
+    const int npair = (nbw + 2 * h - 1) / (2 * h);
+    // X = G(a, b) T(b, b): T(b, b) upper triangular (rows t <= j)
+    for (long long e = gt; e < (long long)npair * h * h; e += GT) {
+      const int p = (int)(e / ((long long)h * h)), r = (int)(e % ((long long)h * h));
+      const int i = r % h, j = r / h, a0 = 2 * p * h, b0 = a0 + h, hb = min(h, nbw - b0);
+      if (hb <= 0 || j >= hb) continue;
+      const double *gr = G + (a0 + i) + (long long)b0 * nbw;
+      const double *tc = Tout + b0 + (long long)(b0 + j) * QR_NB;
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
       int t = 0;
       for (; t + 7 <= j; t += 8) {
         double gv[8], tv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           gv[u] = gr[(long long)(t + u) * nbw];
-          tv[u] = tc[t + u];
+          tv[u] = __ldcg(&tc[t + u]);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc[u & 3] = fma(gv[u], tv[u], acc[u & 3]);
       }
-      for (; t <= j; ++t) acc[0] = fma(gr[(long long)t * nbw], tc[t], acc[0]);
-      Yk[i + (long long)j * kb] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+      for (; t <= j; ++t) acc[0] = fma(gr[(long long)t * nbw], __ldcg(&tc[t]), acc[0]);
+      __stcg(&X[(size_t)p * h * h + i + (size_t)j * h], (acc[0] + acc[1]) + (acc[2] + acc[3]));
     }
-  }
-  unsigned target = gridDim.x;
-  if (!grid_barrier(counter, target, ctrl)) return;
-  for (int k = 1; k < nk; ++k) {
-    const int kb = k * QR_B, bw = min(QR_B, nbw - kb);
-    const double *Yk = Y + (size_t)k * QR_NB * QR_B;
-    for (long long e = gt; e < (long long)kb * bw; e += GT) {
-      const int i = (int)(e % kb), j = (int)(e / kb);
-      // T_out(0:kb, 0:kb) upper triangular: l >= i.  Loads go out 8 at a time
-      // (they come from L2); no line of a column is read before it is final.
-      const double *tr = Tout + i;
-      const double *yc = Yk + (long long)j * kb;
+    tout_barrier(counter, target, ctrl, ok);
+    if (!ok) break;
+    // T(a, b) = -T(a, a) X: T(a, a) upper triangular (columns l >= i)
+    for (long long e = gt; e < (long long)npair * h * h; e += GT) {
+      const int p = (int)(e / ((long long)h * h)), r = (int)(e % ((long long)h * h));
+      const int i = r % h, j = r / h, a0 = 2 * p * h, b0 = a0 + h, hb = min(h, nbw - b0);
+      if (hb <= 0 || j >= hb) continue;
+      const double *tr = Tout + (a0 + i) + (long long)a0 * QR_NB;
+      const double *xc = X + (size_t)p * h * h + (size_t)j * h;
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
       int l = i;
-      for (; l + 7 < kb; l += 8) {
-        double tv[8], yv[8];
+      for (; l + 7 < h; l += 8) {
+        double tv[8], xv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           tv[u] = __ldcg(&tr[(long long)(l + u) * QR_NB]);
-          yv[u] = yc[l + u];
+          xv[u] = __ldcg(&xc[l + u]);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u & 3] = fma(tv[u], yv[u], acc[u & 3]);
+        for (int u = 0; u < 8; ++u) acc[u & 3] = fma(tv[u], xv[u], acc[u & 3]);
       }
-      for (; l < kb; ++l) acc[0] = fma(__ldcg(&tr[(long long)l * QR_NB]), yc[l], acc[0]);
-      __stcg(&Tout[i + (long long)(kb + j) * QR_NB], -((acc[0] + acc[1]) + (acc[2] + acc[3])));
+      for (; l < h; ++l) acc[0] = fma(__ldcg(&tr[(long long)l * QR_NB]), __ldcg(&xc[l]), acc[0]);
+      __stcg(&Tout[(a0 + i) + (long long)(b0 + j) * QR_NB], -((acc[0] + acc[1]) + (acc[2] + acc[3])));
     }
-    if (k + 1 < nk) {
-      target += gridDim.x;
-      if (!grid_barrier(counter, target, ctrl)) return;
-    }
+    tout_barrier(counter, target, ctrl, ok);
   }
 }
 
@@ -354,15 +364,8 @@ int outer_prepare(int rows, int nbw, const double *FJ, int ldf, int m, int first
                   QrMixWork &w, cudaStream_t s) {
   const DeviceInfo *di = device_info();
   const int P = 7 + 8 * (w.S - 1);
-  { LaunchScope ls(KC_OTHER, s, 0.0, 16.0 * rows * (double)nbw, "extract_round_v_kernel");
-    extract_round_v_kernel<<<launch_grid((long long)rows * nbw, di->num_sms * 16), 256, 0, s>>>(rows, nbw, FJ, ldf,
-                                                                                                   w.Vo, m, P); }
-  PURL_CUDA_TRY(cudaGetLastError());
-  { LaunchScope ls(KC_SPLIT, s, 0.0, 8.0 * rows * (double)nbw, "row_exp_kernel");
-    row_exp_kernel<<<launch_grid(rows, di->num_sms * 8), 256, 0, s>>>(rows, nbw, w.Vo, m, w.Vots.scale); }
-  { LaunchScope ls(KC_SPLIT, s, 0.0, (8.0 + 2.0 * w.S) * rows * (double)nbw, "split_rows_t_kernel");
-    split_rows_t_kernel<<<dim3(ceil_div(rows, 32), ceil_div(nbw, 32)), dim3(32, 8), 0, s>>>(rows, nbw, w.Vo, m,
-                                                                                           w.Vots); }
+  { LaunchScope ls(KC_SPLIT, s, 0.0, (24.0 + 2.0 * w.S) * rows * (double)nbw, "outer_v_kernel");
+    outer_v_kernel<<<ceil_div(rows, 32), 256, 0, s>>>(rows, nbw, FJ, ldf, w.Vo, m, P, w.Vots); }
   PURL_CUDA_TRY(cudaGetLastError());
   if (!build_t) return PURL_OK;
   PURL_TRY(split_exact(rows, nbw, w.Vo, m, w.Vos, nullptr, s));
@@ -387,12 +390,12 @@ int outer_prepare(int rows, int nbw, const double *FJ, int ldf, int m, int first
   double *G = w.Tt;  // nbw x nbw, ld nbw
   PURL_TRY(zero_async(w.tcount, sizeof(unsigned), s));
   const double *Tk = w.base.T + (size_t)first_panel * QR_B * QR_B;
-  double *Y = w.Go;  // scratch after the sum: the Y_k
+  double *X = w.Go;  // scratch after the sum: the merges' G(a, b) T(b, b)
   int nbw_ = nbw;
   int grid = di->num_sms;
-  void *args[] = {&nbw_, &G, &Tk, &Tout, &Y, &w.tcount, (void *)&di->ctrl};
+  void *args[] = {&nbw_, &G, &Tk, &Tout, &X, &w.tcount, (void *)&di->ctrl};
   double fl = 0.0;
-  for (int kb = QR_B; kb < nbw; kb += QR_B) fl += 2.0 * kb * QR_B * QR_B / 2 + 1.0 * kb * kb * QR_B;
+  for (int h = QR_B; h < nbw; h *= 2) fl += (double)nbw / (2 * h) * 2.0 * h * h * h;
   LaunchScope ls(KC_OTHER, s, fl, 8.0 * nbw * (double)nbw, "tout_kernel");
   PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)tout_kernel, dim3(grid), dim3(256), args, 0, s));
   return PURL_OK;
