@@ -525,7 +525,12 @@ def _peaks():
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel function, averaged
 # over every launch of one ncu capture of the bench's own step (summary and command under profiles/).
 # It is reported only while the kernel's source file still has the hash it had when captured.
-TRAFFIC = {}
+TRAFFIC = {
+    # 5906 launches of one mixed n = 16384 factorization: 767.97 GB read + 234.00 GB written
+    "tcx_gemm_kernel": {"src": "paper_1812_06007_gb300/csrc/gemm_tcx.cu", "sha16": "e24fc7c040835423",
+                        "bytes_per_launch": 169.65e6,
+                        "profile": "profiles/ncu_tcx_gemm_kernel_traffic_mixed_n16384.md"},
+}
 
 
 def _sha16(path: str) -> str:
