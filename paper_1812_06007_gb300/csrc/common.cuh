@@ -98,6 +98,43 @@ __device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target,
   return s_ok != 0;
 }
 
+// The same barrier in two halves, so that a block can do independent work
+// between arriving and waiting.  grid_arrive: after a __syncthreads that
+// orders the block's writes, thread 0 publishes them and arrives.
+// grid_wait: thread 0 polls (bounded, as grid_barrier) and the block learns
+// the outcome; returns false when the wait gave up or another block aborted.
+__device__ __forceinline__ void grid_arrive(unsigned *counter) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(counter, 1u);
+  }
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned *counter, unsigned target, DeviceControl *ctrl,
+                                          long long spin_limit = kSpinLimit) {
+  __shared__ int s_ok2;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    long long polls = 0;
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+      if (v >= target) break;
+      if ((++polls & 63) == 0 && *(volatile int *)&ctrl->abort) { ok = 0; break; }
+      if (polls > spin_limit) {
+        atomicCAS(&ctrl->status, PURL_OK, PURL_ERR_TIMEOUT);
+        atomicExch(&ctrl->abort, 1);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    s_ok2 = ok;
+  }
+  __syncthreads();
+  return s_ok2 != 0;
+}
+
 // ---------------------------------------------------------- helpers -------
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

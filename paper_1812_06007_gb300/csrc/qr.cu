@@ -116,23 +116,50 @@ __device__ void larft_core(int bw, LarftSmem &L, const double *tau, double *T, b
 }
 
 
-// Rounding, slices, Gram matrix and T of a finished panel (see panel_kernel).
-// Ps holds the block's rows of the factored panel; F has been written.
+// Per-block partial Gram matrix of the rounded vectors, upper triangle column
+// by column (entry (a, j), a <= j, at j (j + 1) / 2 + a).
+__shared__ double g_gacc[QR_B * (QR_B + 1) / 2];
+
+// Column j of the tensor-core QR's panel is final: round it to the grid
+// 2^(vexp - P) into V^ (0 above the diagonal, 1 on it; Vh is the second copy
+// after Ps, or Ps itself) and add this block's rows to the Gram column (a, j),
+// a <= j.
+__device__ void tail_column(int j, int ch, const double *Ps, double *Vh, int r0, int nr, const PanelTail &tl) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double unit = __longlong_as_double((long long)(1023 + tl.vexp - tl.P) << 52);  // 2^(vexp - P)
+  for (int i = tid; i < nr; i += PNT) {
+    const int gi = r0 + i;
+    Vh[j * ch + i] = gi < j ? 0.0 : (gi == j ? 1.0 : (double)fixed_point(Ps[j * ch + i], tl.vexp, tl.P) * unit);
+  }
+  __syncthreads();
+  const double *xj = Vh + j * ch;
+  for (int a = warp; a <= j; a += PW) {
+    const double *xa = Vh + a * ch;
+    double sum = 0.0;
+    for (int i = lane; i < nr; i += 32) sum = fma(xa[i], xj[i], sum);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) g_gacc[j * (j + 1) / 2 + a] = sum;
+  }
+}
+
+// Slices, Gram matrix and T of a finished panel (see panel_kernel).  Ps holds
+// the block's rows of the factored panel, then V^ (columns 0..bw-2 already
+// rounded, with their Gram columns); F has been written.
 __device__ void panel_tail(int rows, int bw, int ch, double *Ps, int c, int P, int r0, int nr, const double *tau,
                            unsigned *counter, DeviceControl *ctrl, const PanelTail &tl) {
   __shared__ LarftSmem L;
   __shared__ unsigned char pa[QR_B * (QR_B + 1) / 2], pb[QR_B * (QR_B + 1) / 2];
-  int *es = reinterpret_cast<int *>(Ps + (size_t)ch * QR_B);  // ch row exponents after the panel
+  double *Vh = tl.overlap ? Ps + (size_t)ch * QR_B : Ps;
+  int *es = reinterpret_cast<int *>(Vh + (size_t)ch * QR_B);  // ch row exponents after V^
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int npairs = bw * (bw + 1) / 2;
-  const double unit = __longlong_as_double((long long)(1023 + tl.vexp - tl.P) << 52);  // 2^(vexp - P)
   (void)rows;
   __syncthreads();
-  // (1) V^: 0 above the diagonal, 1 on it, the rounded vector below
-  for (int e = tid; e < nr * bw; e += PNT) {
-    const int i = e % nr, t = e / nr, gi = r0 + i;
-    const double x = Ps[t * ch + i];
-    Ps[t * ch + i] = gi < t ? 0.0 : (gi == t ? 1.0 : (double)fixed_point(x, tl.vexp, tl.P) * unit);
+  // (1) the last column (every column when V^ is rounded in place)
+  for (int j = tl.overlap ? bw - 1 : 0; j < bw; ++j) {
+    tail_column(j, ch, Ps, Vh, r0, nr, tl);
+    __syncthreads();
   }
   for (int idx = tid; idx < npairs; idx += PNT) {  // upper-triangle pair table (a <= b), column by column
     int b = 0, rem = idx;
@@ -141,6 +168,7 @@ __device__ void panel_tail(int rows, int bw, int ch, double *Ps, int c, int P, i
     pb[idx] = (unsigned char)b;
   }
   __syncthreads();
+  Ps = Vh;  // the slices below read V^
   // (2) natural slices, exponent vexp per column; (3) row exponents
   for (int e = tid; e < nr * bw; e += PNT) {
     const int i = e % nr, t = e / nr;
@@ -161,15 +189,10 @@ __device__ void panel_tail(int rows, int bw, int ch, double *Ps, int c, int P, i
     write_fixed_slices(Ps[t * ch + i], es[i], tl.vts.base + t + (long long)(r0 + i) * tl.vts.ld, tl.vts.plane,
                        tl.vts.S);
   }
-  // (4) this block's part of the Gram matrix: one warp per entry, lanes along rows
-  for (int idx = warp; idx < npairs; idx += PW) {
-    const double *xa = Ps + pa[idx] * ch, *xb = Ps + pb[idx] * ch;
-    double sum = 0.0;
-    for (int i = lane; i < nr; i += 32) sum = fma(xa[i], xb[i], sum);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) __stcg(&tl.gpart[(size_t)c * npairs + idx], sum);
-  }
+  // (4) this block's part of the Gram matrix (formed column by column)
+  for (int idx = tid; idx < npairs; idx += PNT) __stcg(&tl.gpart[(size_t)c * npairs + idx], g_gacc[idx]);
+  (void)lane;
+  (void)warp;
   if (!grid_barrier(counter, (unsigned)(bw + 1) * P, ctrl)) return;
   // (5) distributed sum over the blocks in a fixed order: warp w of block c
   // takes entry c + P w
@@ -241,8 +264,17 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
     }
     if (k >= r0 && k < r0 + nr)
       for (int t = k + tid; t < bw; t += PNT) __stcg(&rk[t], Ps[t * ch + (k - r0)]);
-    // (b) one barrier per column
-    if (!grid_barrier(counter, (unsigned)(k + 1) * P, ctrl)) return;
+    // (b) one barrier per column.  The tensor-core QR's panel rounds the
+    // previous column's vector and forms its Gram column between arriving and
+    // waiting (the FP64 pipe is otherwise idle there).
+    if constexpr (TAIL) {
+      __syncthreads();
+      grid_arrive(counter);
+      if (tail.overlap && k > 0) tail_column(k - 1, ch, Ps, Ps + (size_t)ch * QR_B, r0, nr, tail);
+      if (!grid_wait(counter, (unsigned)(k + 1) * P, ctrl)) return;
+    } else {
+      if (!grid_barrier(counter, (unsigned)(k + 1) * P, ctrl)) return;
+    }
     // (c) every block reduces the partials in the same fixed order: thread
     // (t = tid % 32, j = tid / 32) sums blocks j, j + 8, ... with independent
     // loads (one L2 round trip, not one per block), warp 0 adds the 8 partial
@@ -567,13 +599,21 @@ int panel_factor_tail(int rows, int bw, double *Fp, int ldf, double *taup, unsig
   if (!di) return PURL_ERR_CUDA;
   int P = panel_blocks(rows, di);
   int ch = ceil_div(rows, P);
-  // the panel's rows, then one int per row (the transposed slices' exponents)
-  size_t smem = (size_t)ch * QR_B * sizeof(double) + align_up((size_t)ch * sizeof(int), 16);
+  // the panel's rows, their rounded copy V^, then one int per row (the
+  // transposed slices' exponents); without room for the copy, V^ is rounded in
+  // place at the end and its Gram columns formed there
+  PanelTail tl = tail;
+  const size_t es_bytes = align_up((size_t)ch * sizeof(int), 16);
+  size_t smem = 2 * (size_t)ch * QR_B * sizeof(double) + es_bytes;
+  tl.overlap = 1;
+  if (panel_capacity<true>(di, smem) < P) {
+    smem = (size_t)ch * QR_B * sizeof(double) + es_bytes;
+    tl.overlap = 0;
+  }
   int cap = panel_capacity<true>(di, smem);
   if (cap < P) return PURL_ERR_UNSUPPORTED;
   int ldv = rows;
   long long ldf_ll = ldf, ldv_ll = ldv;
-  PanelTail tl = tail;
   void *args[] = {&rows, &bw, &ch, &Fp, &ldf_ll, &w.Vb, &ldv_ll, &taup, &w.part, &w.rowk, &counter,
                   (void *)&di->ctrl, &tl};
   // panel flops plus the Gram matrix of the rounded vectors

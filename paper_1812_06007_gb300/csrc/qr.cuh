@@ -28,6 +28,7 @@ struct QrWork {
 // column) and the T factor.
 struct PanelTail {
   int vexp = 1, P = 31;
+  int overlap = 1;  // set by panel_factor_tail: V^ kept in a second shared copy (else rounded in place)
   Slices vs, vts;
   double *gpart = nullptr, *G = nullptr, *T = nullptr;
 };

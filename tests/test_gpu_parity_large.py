@@ -1,9 +1,11 @@
 """Elementwise oracle parity at the sizes where the GPU path changes code path.
 
 - The Householder panel kernel launches ceil(rows / 64) cooperative blocks,
-  capped at 160: beyond 10240 rows every block owns a slab of more than 64
-  rows.  Tall-skinny QRs of 20000 x 64 and 40000 x 96 take that path, as the
-  n = 16384 factorizations of the benchmark do.
+  capped at the SM count: beyond ~10K rows every block owns a slab of more
+  than 64 rows.  Tall-skinny QRs of 20000 x 64 and 40000 x 96 take that path,
+  as the n = 16384 factorizations of the benchmark do; at 70000 rows the
+  tensor-core QR's panel no longer has room for a second shared copy of the
+  rounded vectors and rounds them in place.
 - The blocked QRs group 32-column panels into 512-column outer blocks whose
   aggregated reflectors update the rest of the matrix: n = 1536 crosses three
   outer blocks (the smaller parity tests cross at most two).
@@ -66,7 +68,7 @@ def _check_qr(mode, M, Q, R):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("m,n", [(20000, 64), (40000, 96), (10241, 33)])
+@pytest.mark.parametrize("m,n", [(20000, 64), (40000, 96), (10241, 33), (70000, 40)])
 def test_tall_skinny_qr_on_capped_panel_grid(B, mode, m, n):
     M = np.random.default_rng(m + n).standard_normal((m, n))
     Q, R = (_host(x) for x in B.purl_qr(_dev(M), mode=_mode(B, mode)))
