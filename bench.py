@@ -920,6 +920,7 @@ def run_adjoint(a):
         step()
     torch.cuda.synchronize()
     B.purl_profile_reset()
+    B.purl_profile_set_stride(8)
     B.purl_profile_enable(True)
     launches0 = B.purl_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1048,6 +1049,7 @@ def run_rsvd(a):
         U, S, V = B.purl_rsvd(A, l, q, W.SEED_G, reorth, workspace=ws, stream=stream)
     torch.cuda.synchronize()
     B.purl_profile_reset()
+    B.purl_profile_set_stride(8)
     B.purl_profile_enable(True)
     launches0 = B.purl_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
