@@ -123,20 +123,25 @@ __shared__ double g_gacc[QR_B * (QR_B + 1) / 2];
 // Column j of the tensor-core QR's panel is final: round it to the grid
 // 2^(vexp - P) into V^ (0 above the diagonal, 1 on it; Vh is the second copy
 // after Ps, or Ps itself) and add this block's rows to the Gram column (a, j),
-// a <= j.
-__device__ void tail_column(int j, int ch, const double *Ps, double *Vh, int r0, int nr, const PanelTail &tl) {
+// a <= j.  Entries of V are at most 1 in magnitude, so with Real = float and
+// P = 31 (or less) every rounded entry is again a float: the grid is no finer
+// than a float's spacing wherever the float has bits below the grid.  The
+// products of two floats are exact in FP64; the sums are FP64.
+template <typename Real>
+__device__ void tail_column(int j, int ch, const Real *Ps, Real *Vh, int r0, int nr, const PanelTail &tl) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double unit = __longlong_as_double((long long)(1023 + tl.vexp - tl.P) << 52);  // 2^(vexp - P)
   for (int i = tid; i < nr; i += PNT) {
     const int gi = r0 + i;
-    Vh[j * ch + i] = gi < j ? 0.0 : (gi == j ? 1.0 : (double)fixed_point(Ps[j * ch + i], tl.vexp, tl.P) * unit);
+    Vh[j * ch + i] = gi < j ? Real(0) : (gi == j ? Real(1)
+                                                 : (Real)((double)fixed_point((double)Ps[j * ch + i], tl.vexp, tl.P) * unit));
   }
   __syncthreads();
-  const double *xj = Vh + j * ch;
+  const Real *xj = Vh + j * ch;
   for (int a = warp; a <= j; a += PW) {
-    const double *xa = Vh + a * ch;
+    const Real *xa = Vh + a * ch;
     double sum = 0.0;
-    for (int i = lane; i < nr; i += 32) sum = fma(xa[i], xj[i], sum);
+    for (int i = lane; i < nr; i += 32) sum = fma((double)xa[i], (double)xj[i], sum);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) g_gacc[j * (j + 1) / 2 + a] = sum;
@@ -145,16 +150,17 @@ __device__ void tail_column(int j, int ch, const double *Ps, double *Vh, int r0,
 
 // Slices, Gram matrix and T of a finished panel (see panel_kernel).  Ps holds
 // the block's rows of the factored panel, then V^ (columns 0..bw-2 already
-// rounded, with their Gram columns); F has been written.
-__device__ void panel_tail(int rows, int bw, int ch, double *Ps, int c, int P, int r0, int nr, const double *tau,
-                           unsigned *counter, DeviceControl *ctrl, const PanelTail &tl) {
+// rounded, with their Gram columns); F has been written.  `nbar` grid
+// barriers came before.
+template <typename Real>
+__device__ void panel_tail(int bw, int ch, Real *Ps, int c, int P, int r0, int nr, const double *tau,
+                           unsigned *counter, DeviceControl *ctrl, const PanelTail &tl, unsigned nbar) {
   __shared__ LarftSmem L;
   __shared__ unsigned char pa[QR_B * (QR_B + 1) / 2], pb[QR_B * (QR_B + 1) / 2];
-  double *Vh = tl.overlap ? Ps + (size_t)ch * QR_B : Ps;
+  Real *Vh = tl.overlap ? Ps + (size_t)ch * QR_B : Ps;
   int *es = reinterpret_cast<int *>(Vh + (size_t)ch * QR_B);  // ch row exponents after V^
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int npairs = bw * (bw + 1) / 2;
-  (void)rows;
   __syncthreads();
   // (1) the last column (every column when V^ is rounded in place)
   for (int j = tl.overlap ? bw - 1 : 0; j < bw; ++j) {
@@ -168,17 +174,16 @@ __device__ void panel_tail(int rows, int bw, int ch, double *Ps, int c, int P, i
     pb[idx] = (unsigned char)b;
   }
   __syncthreads();
-  Ps = Vh;  // the slices below read V^
   // (2) natural slices, exponent vexp per column; (3) row exponents
   for (int e = tid; e < nr * bw; e += PNT) {
     const int i = e % nr, t = e / nr;
-    write_fixed_slices(Ps[t * ch + i], tl.vexp, tl.vs.base + (r0 + i) + (long long)t * tl.vs.ld, tl.vs.plane,
-                       tl.vs.S);
+    write_fixed_slices((double)Vh[t * ch + i], tl.vexp, tl.vs.base + (r0 + i) + (long long)t * tl.vs.ld,
+                       tl.vs.plane, tl.vs.S);
   }
   if (c == 0 && tid < bw) tl.vs.scale[tid] = tl.vexp;
   for (int i = tid; i < nr; i += PNT) {
     unsigned long long mx = 0;
-    for (int t = 0; t < bw; ++t) mx = max(mx, abs_bits(Ps[t * ch + i]));
+    for (int t = 0; t < bw; ++t) mx = max(mx, abs_bits((double)Vh[t * ch + i]));
     es[i] = exp_above_bits(mx);
     tl.vts.scale[r0 + i] = es[i];
   }
@@ -186,24 +191,25 @@ __device__ void panel_tail(int rows, int bw, int ch, double *Ps, int c, int P, i
   // transposed slices, the lanes along the columns
   for (int e = tid; e < nr * bw; e += PNT) {
     const int t = e % bw, i = e / bw;
-    write_fixed_slices(Ps[t * ch + i], es[i], tl.vts.base + t + (long long)(r0 + i) * tl.vts.ld, tl.vts.plane,
-                       tl.vts.S);
+    write_fixed_slices((double)Vh[t * ch + i], es[i], tl.vts.base + t + (long long)(r0 + i) * tl.vts.ld,
+                       tl.vts.plane, tl.vts.S);
   }
   // (4) this block's part of the Gram matrix (formed column by column)
   for (int idx = tid; idx < npairs; idx += PNT) __stcg(&tl.gpart[(size_t)c * npairs + idx], g_gacc[idx]);
-  (void)lane;
-  (void)warp;
-  if (!grid_barrier(counter, (unsigned)(bw + 1) * P, ctrl)) return;
+  if (!grid_barrier(counter, (nbar + 1) * P, ctrl)) return;
   // (5) distributed sum over the blocks in a fixed order: warp w of block c
   // takes entry c + P w
-  for (int idx = c + P * warp; idx < npairs; idx += P * PW) {
-    double sum = 0.0;
-    for (int z = lane; z < P; z += 32) sum += __ldcg(&tl.gpart[(size_t)z * npairs + idx]);
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int idx = c + P * warp; idx < npairs; idx += P * PW) {
+      double sum = 0.0;
+      for (int z = lane; z < P; z += 32) sum += __ldcg(&tl.gpart[(size_t)z * npairs + idx]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) __stcg(&tl.G[idx], sum);
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) __stcg(&tl.G[idx], sum);
+    }
   }
-  if (!grid_barrier(counter, (unsigned)(bw + 2) * P, ctrl)) return;
+  if (!grid_barrier(counter, (nbar + 2) * P, ctrl)) return;
   if (c != 0) return;
   // (6) block 0: T from the Gram matrix (tau_k = 2 / ||v^_k||^2)
   for (int e = tid; e < QR_B * QR_B; e += PNT) L.Gm[e % QR_B][e / QR_B] = 0.0;
@@ -221,42 +227,98 @@ __device__ void panel_tail(int rows, int bw, int ch, double *Ps, int c, int P, i
 // F points at F(j0, j0); the panel has `rows` rows and `bw` <= QR_B columns.
 // Block c owns panel rows [c*ch, min(rows, (c+1)*ch)).
 //
+// Real is the arithmetic of the column loop.  Real = double: the FP64 panel.
+// Real = float (the tensor-core QR at up to 4 slices): the rows are kept and
+// updated in FP32 and the partial sums are FP32, while each reflector's norm,
+// sign, beta and tau are formed in FP64 and F(k,k) = beta is written from
+// FP64.  Each column is first scaled by a power of two that brings its largest
+// entry into [1, 2) (one extra grid barrier), so that FP32's exponent range
+// never limits the panel; the reflectors are scale-invariant and R's entries
+// are scaled back when written.
+//
 // TAIL (the tensor-core QR's panel): after the columns, the blocks also round
 // the Householder vectors to the grid 2^(vexp - P) (V^), write V^'s fixed-point
 // slices (natural, exponent vexp per column; transposed, the exponent of each
 // row's largest entry), form the FP64 Gram matrix V^T V^ (per-block partials,
 // one grid barrier, a distributed sum, another barrier) and block 0 builds T
 // from it with tau_k = 2 / ||v^_k||^2.  Without TAIL the explicit V goes to Vb.
-template <bool TAIL>
+template <bool TAIL, typename Real>
 __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, double *F,
                                                     long long ldf, double *Vb, long long ldv,
                                                     double *tau, double *part, double *rowk,
                                                     unsigned *counter, DeviceControl *ctrl, PanelTail tail) {
-  extern __shared__ double Ps[];  // ch x QR_B, column-major (column t at Ps + t*ch)
-  __shared__ double s_w[QR_B];
+  constexpr bool SCALED = sizeof(Real) == 4;
+  constexpr unsigned base = SCALED ? 1u : 0u;  // grid barriers before column 0
+  extern __shared__ __align__(16) unsigned char p_smem[];
+  Real *Ps = reinterpret_cast<Real *>(p_smem);  // ch x QR_B, column-major (column t at Ps + t*ch)
+  __shared__ Real s_w[QR_B];
   __shared__ double s_par[4];     // beta, -, tau, 1/v0
-  __shared__ double s_red[PW][32];
+  __shared__ double s_beta[QR_B];
+  __shared__ double s_up[QR_B];   // per-column factor back to F's scale (scaled panels)
+  __shared__ Real s_red[PW][32];
   const int P = gridDim.x;
   const int c = blockIdx.x;
   const int r0 = c * ch;
   const int nr = max(0, min(rows, r0 + ch) - r0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  Real *parts = reinterpret_cast<Real *>(part);
+  Real *rows_k = reinterpret_cast<Real *>(rowk);
 
-  for (int e = tid; e < ch * bw; e += PNT) {
-    int i = e % ch, t = e / ch;
-    Ps[t * ch + i] = (i < nr) ? F[(r0 + i) + t * ldf] : 0.0;
+  if constexpr (SCALED) {
+    // (0) the largest exponent field of each column over all blocks
+    __shared__ int s_ex[PW][32];
+    int *pe = reinterpret_cast<int *>(parts + (size_t)2 * P * QR_B);
+    for (int t = warp; t < bw; t += PW) {
+      unsigned mx = 0;
+      for (int i = lane; i < nr; i += 32)
+        mx = max(mx, (unsigned)((__double_as_longlong(F[(r0 + i) + t * ldf]) >> 52) & 0x7ff));
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (lane == 0) __stcg(&pe[(size_t)c * QR_B + t], (int)mx);
+    }
+    if (!grid_barrier(counter, (unsigned)P, ctrl)) return;
+    {
+      const int t = tid & 31, j = tid >> 5;
+      int v[kPanelMaxBlocks / PW];
+#pragma unroll
+      for (int u = 0; u < kPanelMaxBlocks / PW; ++u) {
+        const int b = j + u * PW;
+        v[u] = (t < bw && b < P) ? __ldcg(&pe[(size_t)b * QR_B + t]) : 0;
+      }
+      int mx = 0;
+#pragma unroll
+      for (int u = 0; u < kPanelMaxBlocks / PW; ++u) mx = max(mx, v[u]);
+      s_ex[j][t] = mx;
+    }
+    __syncthreads();
+    if (tid < QR_B) {
+      int E = 0;
+#pragma unroll
+      for (int j = 0; j < PW; ++j) E = max(E, s_ex[j][tid]);
+      s_up[tid] = ldexp(1.0, E - 1023);  // largest entry / 2^(E-1023) lies in [1, 2)
+      s_ex[0][tid] = E;
+    }
+    __syncthreads();
+    for (int e = tid; e < ch * bw; e += PNT) {
+      const int i = e % ch, t = e / ch;
+      Ps[t * ch + i] = (i < nr) ? (Real)ldexp(F[(r0 + i) + t * ldf], 1023 - s_ex[0][t]) : Real(0);
+    }
+  } else {
+    for (int e = tid; e < ch * bw; e += PNT) {
+      const int i = e % ch, t = e / ch;
+      Ps[t * ch + i] = (i < nr) ? (Real)F[(r0 + i) + t * ldf] : Real(0);
+    }
   }
   __syncthreads();
 
   for (int k = 0; k < bw; ++k) {
     const int buf = k & 1;
-    double *pb = part + (size_t)buf * P * QR_B;
-    double *rk = rowk + (size_t)buf * QR_B;
+    Real *pb = parts + (size_t)buf * P * QR_B;
+    Real *rk = rows_k + (size_t)buf * QR_B;
     // rows of this block strictly below row k
     const int i_lo = max(0, k + 1 - r0);
     // (a) partials: t == k gives sum x_i^2, t > k gives sum x_i a_it
     for (int t = k + warp; t < bw; t += PW) {
-      double s = 0.0;
+      Real s = 0;
       for (int i = i_lo + lane; i < nr; i += 32) s += Ps[k * ch + i] * Ps[t * ch + i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -267,30 +329,31 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
     // (b) one barrier per column.  The tensor-core QR's panel rounds the
     // previous column's vector and forms its Gram column between arriving and
     // waiting (the FP64 pipe is otherwise idle there).
+    const unsigned target = (unsigned)(k + 1 + base) * P;
     if constexpr (TAIL) {
       __syncthreads();
       grid_arrive(counter);
       if (tail.overlap && k > 0) tail_column(k - 1, ch, Ps, Ps + (size_t)ch * QR_B, r0, nr, tail);
-      if (!grid_wait(counter, (unsigned)(k + 1) * P, ctrl)) return;
+      if (!grid_wait(counter, target, ctrl)) return;
     } else {
-      if (!grid_barrier(counter, (unsigned)(k + 1) * P, ctrl)) return;
+      if (!grid_barrier(counter, target, ctrl)) return;
     }
     // (c) every block reduces the partials in the same fixed order: thread
     // (t = tid % 32, j = tid / 32) sums blocks j, j + 8, ... with independent
     // loads (one L2 round trip, not one per block), warp 0 adds the 8 partial
     // sums and forms the reflector.  Row k is fetched in the same round trip.
-    const double rkt = (warp == 0 && lane < bw) ? __ldcg(&rk[lane]) : 0.0;
+    const Real rkt = (warp == 0 && lane < bw) ? __ldcg(&rk[lane]) : Real(0);
     {
       const int t = tid & 31, j = tid >> 5;
-      double acc = 0.0;
+      Real acc = 0;
       if (t >= k && t < bw) {
         // all of this thread's partials are loaded before any is added, so
         // the loads share one round trip (P <= kPanelMaxBlocks)
-        double v[kPanelMaxBlocks / PW];
+        Real v[kPanelMaxBlocks / PW];
 #pragma unroll
         for (int u = 0; u < kPanelMaxBlocks / PW; ++u) {
           const int b = j + u * PW;
-          v[u] = (b < P) ? __ldcg(&pb[(size_t)b * QR_B + t]) : 0.0;
+          v[u] = (b < P) ? __ldcg(&pb[(size_t)b * QR_B + t]) : Real(0);
         }
 #pragma unroll
         for (int u = 0; u < kPanelMaxBlocks / PW; ++u) acc += v[u];
@@ -299,11 +362,12 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
     }
     __syncthreads();
     if (warp == 0) {
-      double S = 0.0;
+      Real S = 0;
 #pragma unroll
-      for (int j = 0; j < PW; ++j) S += s_red[j][lane];  // s_w-like: S(k) = sigma, S(t>k) = dot_t
-      const double sigma = __shfl_sync(0xffffffffu, S, k);
-      const double x0 = __shfl_sync(0xffffffffu, rkt, k);
+      for (int j = 0; j < PW; ++j) S += s_red[j][lane];  // S(k) = sigma, S(t>k) = dot_t
+      // the reflector's parameters in FP64
+      const double sigma = (double)__shfl_sync(0xffffffffu, S, k);
+      const double x0 = (double)__shfl_sync(0xffffffffu, rkt, k);
       double beta, tk, inv_v0;
       if (sigma == 0.0) {
         beta = x0; tk = 0.0; inv_v0 = 1.0;
@@ -318,25 +382,27 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
         tk = fabs(v0) * v0 * r;
       }
       // w_t = tau (a_kt + v(k+1:)^T a_t) with v(k+1:) = x(k+1:)/v0
-      if (lane > k && lane < bw) s_w[lane] = tk * (rkt + S * inv_v0);
+      if (lane > k && lane < bw) s_w[lane] = (Real)(tk * ((double)rkt + (double)S * inv_v0));
       if (lane == 0) {
         s_par[0] = beta; s_par[2] = tk; s_par[3] = inv_v0;
+        s_beta[k] = beta;
         if (c == 0) tau[k] = tk;
       }
     }
     __syncthreads();
-    const double beta = s_par[0], tk = s_par[2], inv_v0 = s_par[3];
+    const double tk = s_par[2];
     if (tk != 0.0) {
-      for (int i = i_lo + tid; i < nr; i += PNT) Ps[k * ch + i] *= inv_v0;
+      const Real iv = (Real)s_par[3];
+      for (int i = i_lo + tid; i < nr; i += PNT) Ps[k * ch + i] *= iv;
       __syncthreads();
-      if (k >= r0 && k < r0 + nr && tid == 0) Ps[k * ch + (k - r0)] = beta;
+      if (k >= r0 && k < r0 + nr && tid == 0) Ps[k * ch + (k - r0)] = (Real)s_par[0];
       const int ncol = bw - k - 1;
       const int i_from = max(0, k - r0);  // include row k itself (v_k = 1)
       const int span = nr - i_from;
       if (ncol > 0 && span > 0) {
         for (int e = tid; e < ncol * span; e += PNT) {
           int t = k + 1 + e / span, i = i_from + e % span;
-          double v = (r0 + i == k) ? 1.0 : Ps[k * ch + i];
+          Real v = (r0 + i == k) ? Real(1) : Ps[k * ch + i];
           Ps[t * ch + i] -= s_w[t] * v;
         }
       }
@@ -347,11 +413,15 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
   for (int e = tid; e < nr * bw; e += PNT) {
     int i = e % nr, t = e / nr;
     int gi = r0 + i;
-    double x = Ps[t * ch + i];
+    double x = (double)Ps[t * ch + i];
+    if constexpr (SCALED) {  // R back to F's scale (beta from FP64); V is scale-free
+      if (gi == t) x = s_beta[t];
+      if (gi <= t) x *= s_up[t];
+    }
     F[gi + t * ldf] = x;
     if constexpr (!TAIL) Vb[gi + t * ldv] = (gi < t) ? 0.0 : (gi == t ? 1.0 : x);
   }
-  if constexpr (TAIL) panel_tail(rows, bw, ch, Ps, c, P, r0, nr, tau, counter, ctrl, tail);
+  if constexpr (TAIL) panel_tail(bw, ch, Ps, c, P, r0, nr, tau, counter, ctrl, tail, (unsigned)bw + base);
 }
 
 // ------------------------------------------------------------ T factor ----
@@ -504,14 +574,14 @@ int grid_for(long long total, const DeviceInfo *di) {
 // end (capacity only falls as shared memory grows); the kernel's dynamic
 // shared-memory limit is only ever raised.  Returns 0 when `smem` does not fit
 // beside the kernel's static shared memory.
-template <bool TAIL>
+template <bool TAIL, typename Real>
 int panel_capacity(const DeviceInfo *di, size_t smem) {
   static std::mutex mu;
   static std::map<std::pair<int, size_t>, int> cache;
   static std::map<int, size_t> limit;
   std::lock_guard<std::mutex> lock(mu);
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, panel_kernel<TAIL>) != cudaSuccess) return 0;
+  if (cudaFuncGetAttributes(&fa, panel_kernel<TAIL, Real>) != cudaSuccess) return 0;
   const size_t room = (size_t)di->max_smem_optin > fa.sharedSizeBytes ? di->max_smem_optin - fa.sharedSizeBytes : 0;
   if (smem > room) return 0;
   size_t step = (smem + 4095) / 4096 * 4096;
@@ -521,12 +591,12 @@ int panel_capacity(const DeviceInfo *di, size_t smem) {
   if (it != cache.end()) return it->second;
   size_t &lim = limit[di->device];
   if (step > 48 * 1024 - fa.sharedSizeBytes && step > lim) {
-    if (cudaFuncSetAttribute(panel_kernel<TAIL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step) != cudaSuccess)
+    if (cudaFuncSetAttribute(panel_kernel<TAIL, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step) != cudaSuccess)
       return 0;
     lim = step;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel<TAIL>, PNT, step) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel<TAIL, Real>, PNT, step) != cudaSuccess) return 0;
   const int cap = per_sm * di->num_sms;
   cache[key] = cap;
   return cap;
@@ -581,7 +651,7 @@ int panel_factor(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *
   int P = panel_blocks(rows, di);
   int ch = ceil_div(rows, P);
   size_t smem = (size_t)ch * QR_B * sizeof(double);
-  int cap = panel_capacity<false>(di, smem);
+  int cap = panel_capacity<false, double>(di, smem);
   if (cap < P) return PURL_ERR_UNSUPPORTED;
   int ldv = rows;
   long long ldf_ll = ldf, ldv_ll = ldv;
@@ -589,14 +659,13 @@ int panel_factor(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *
   void *args[] = {&rows, &bw, &ch, &Fp, &ldf_ll, &w.Vb, &ldv_ll, &taup, &w.part, &w.rowk, &counter,
                   (void *)&di->ctrl, &none};
   LaunchScope ls(KC_PANEL, s, 2.0 * rows * bw * (double)bw, 16.0 * rows * bw, "panel_kernel");
-  PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel<false>, dim3(P), dim3(PNT), args, smem, s));
+  PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel<false, double>, dim3(P), dim3(PNT), args, smem, s));
   return PURL_OK;
 }
 
-int panel_factor_tail(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *counter, QrWork &w,
-                      const PanelTail &tail, cudaStream_t s) {
-  const DeviceInfo *di = device_info();
-  if (!di) return PURL_ERR_CUDA;
+template <typename Real>
+static int panel_tail_launch(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *counter, QrWork &w,
+                             const PanelTail &tail, const DeviceInfo *di, cudaStream_t s) {
   int P = panel_blocks(rows, di);
   int ch = ceil_div(rows, P);
   // the panel's rows, their rounded copy V^, then one int per row (the
@@ -604,13 +673,13 @@ int panel_factor_tail(int rows, int bw, double *Fp, int ldf, double *taup, unsig
   // place at the end and its Gram columns formed there
   PanelTail tl = tail;
   const size_t es_bytes = align_up((size_t)ch * sizeof(int), 16);
-  size_t smem = 2 * (size_t)ch * QR_B * sizeof(double) + es_bytes;
+  size_t smem = 2 * (size_t)ch * QR_B * sizeof(Real) + es_bytes;
   tl.overlap = 1;
-  if (panel_capacity<true>(di, smem) < P) {
-    smem = (size_t)ch * QR_B * sizeof(double) + es_bytes;
+  if (panel_capacity<true, Real>(di, smem) < P) {
+    smem = (size_t)ch * QR_B * sizeof(Real) + es_bytes;
     tl.overlap = 0;
   }
-  int cap = panel_capacity<true>(di, smem);
+  int cap = panel_capacity<true, Real>(di, smem);
   if (cap < P) return PURL_ERR_UNSUPPORTED;
   int ldv = rows;
   long long ldf_ll = ldf, ldv_ll = ldv;
@@ -619,8 +688,18 @@ int panel_factor_tail(int rows, int bw, double *Fp, int ldf, double *taup, unsig
   // panel flops plus the Gram matrix of the rounded vectors
   LaunchScope ls(KC_PANEL, s, 2.0 * rows * bw * (double)bw + (double)rows * bw * (bw + 1), 16.0 * rows * bw,
                  "panel_kernel");
-  PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel<true>, dim3(P), dim3(PNT), args, smem, s));
+  PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel<true, Real>, dim3(P), dim3(PNT), args, smem, s));
   return PURL_OK;
+}
+
+// The panel runs in FP32 (FP64 reflector parameters) when V^ carries at most
+// 31 bits (up to 4 slices), in FP64 otherwise.
+int panel_factor_tail(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *counter, QrWork &w,
+                      const PanelTail &tail, cudaStream_t s) {
+  const DeviceInfo *di = device_info();
+  if (!di) return PURL_ERR_CUDA;
+  if (tail.P <= 31) return panel_tail_launch<float>(rows, bw, Fp, ldf, taup, counter, w, tail, di, s);
+  return panel_tail_launch<double>(rows, bw, Fp, ldf, taup, counter, w, tail, di, s);
 }
 
 // T factor of one panel from split-K partials of its Gram matrix V^T V.
