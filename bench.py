@@ -612,6 +612,16 @@ def roofline(prof, named, steps, mode, sm_mhz=None, sms=152):
                      "frac": achieved / peak, "peak_source": f"{src} bf16 sustained (cuBLAS)",
                      "flops_counted": "issued: 2 m n k per BF16 slice pair"})
         return base
+    if name == "panel_kernel" and mode in ("mixed", "mixed16", "fp32"):
+        # the tensor-core QR's panel at up to 4 slices computes in FP32 (its reflector
+        # parameters in FP64, its Gram matrix in integers)
+        achieved = st["flops"] / sec / 1e12
+        peak = FP32_LANES * 2 * (sm_mhz or 1920.0) * 1e6 / 1e12 * sms / 152
+        base.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak,
+                     "peak_source": f"FP32 FFMA: {sms} SMs x 128 lanes x 2 flops x "
+                                    f"{(sm_mhz or 1920.0):.0f} MHz (sampled SM clock)"})
+        return base
     if name in ("panel_kernel", "gemm_f64_kernel", "gram_kernel") or name.startswith("gemm_f64"):
         achieved = st["flops"] / sec / 1e12
         peak = fp64_peak_tflops(sm_mhz, sms)

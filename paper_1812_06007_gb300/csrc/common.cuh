@@ -66,16 +66,26 @@ constexpr long long kSpinLimit = 1LL << 23;
 // ------------------------------------------------------ grid barrier ------
 // Barrier among the `nblocks` co-resident blocks of a cooperative launch.
 // `counter` starts at 0 for the launch; the i-th barrier (i = 0, 1, ...)
-// completes when the counter reaches (i+1) * nblocks.  Every wait is bounded:
-// on expiry the block records PURL_ERR_TIMEOUT, raises the abort flag and
-// returns false; callers then leave the kernel.
-__device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target,
-                                             DeviceControl *ctrl, long long spin_limit = kSpinLimit) {
-  __syncthreads();
-  __shared__ int s_ok;
+// completes when the counter reaches (i+1) * nblocks.  Arriving is a release
+// reduction by thread 0 after a __syncthreads (publishing every write the
+// block made before it), waiting an acquire poll by thread 0 followed by a
+// __syncthreads (so every thread of the block sees what the others
+// published).  Every wait is bounded: on expiry the block records
+// PURL_ERR_TIMEOUT, raises the abort flag and returns false; callers then
+// leave the kernel.
+//
+// In two halves, so that a block can do independent work between arriving and
+// waiting.  grid_arrive: after a __syncthreads that orders the block's
+// writes, thread 0 arrives.  grid_wait: thread 0 polls and the block learns
+// the outcome; returns false when the wait gave up or another block aborted.
+__device__ __forceinline__ void grid_arrive(unsigned *counter) {
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned *counter, unsigned target, DeviceControl *ctrl,
+                                          long long spin_limit = kSpinLimit) {
+  __shared__ int s_ok2;
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(counter, 1u);
     int ok = 1;
     long long polls = 0;
     while (true) {
@@ -91,48 +101,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target,
         break;
       }
     }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// The same barrier in two halves, so that a block can do independent work
-// between arriving and waiting.  grid_arrive: after a __syncthreads that
-// orders the block's writes, thread 0 publishes them and arrives.
-// grid_wait: thread 0 polls (bounded, as grid_barrier) and the block learns
-// the outcome; returns false when the wait gave up or another block aborted.
-__device__ __forceinline__ void grid_arrive(unsigned *counter) {
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(counter, 1u);
-  }
-}
-
-__device__ __forceinline__ bool grid_wait(unsigned *counter, unsigned target, DeviceControl *ctrl,
-                                          long long spin_limit = kSpinLimit) {
-  __shared__ int s_ok2;
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    long long polls = 0;
-    while (true) {
-      unsigned v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
-      if (v >= target) break;
-      if ((++polls & 63) == 0 && *(volatile int *)&ctrl->abort) { ok = 0; break; }
-      if (polls > spin_limit) {
-        atomicCAS(&ctrl->status, PURL_OK, PURL_ERR_TIMEOUT);
-        atomicExch(&ctrl->abort, 1);
-        ok = 0;
-        break;
-      }
-    }
-    __threadfence();
     s_ok2 = ok;
   }
   __syncthreads();
   return s_ok2 != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target, DeviceControl *ctrl,
+                                             long long spin_limit = kSpinLimit) {
+  __syncthreads();
+  grid_arrive(counter);
+  return grid_wait(counter, target, ctrl, spin_limit);
 }
 
 // ---------------------------------------------------------- helpers -------

@@ -53,6 +53,7 @@ __device__ __forceinline__ unsigned short bf16_bits_small(int d) {
 }
 
 // Write the S digits of x (|x| < 2^e) as BF16 slices: slice s at dst[s * plane],
+// from N = round(x 2^(P - e)) (write_int_slices takes N itself, |N| <= 2^P),
 // S <= 8 (P = 7 + 8(S-1) <= 63 keeps N in a 64-bit integer).  The balanced
 // base-256 digits of N are read off M = N + 128 (1 + 2^8 + ... + 2^(8(S-2))):
 // byte j of M minus 128 is the digit of weight 2^(8j) for j < S-1, and M
@@ -61,8 +62,7 @@ __device__ __forceinline__ unsigned short bf16_bits_small(int d) {
 // modulo 2^64 (for S = 8 it can pass 2^63), so the top digit t in [-128, 128]
 // is read from its byte, which leaves only t = +-128 ambiguous; N's sign
 // settles that.
-__device__ __forceinline__ void write_fixed_slices(double x, int e, __nv_bfloat16 *dst, long long plane, int S) {
-  const long long n = fixed_point(x, e, 7 + 8 * (S - 1));
+__device__ __forceinline__ void write_int_slices(long long n, __nv_bfloat16 *dst, long long plane, int S) {
   const unsigned long long bias = 0x0080808080808080ULL >> (8 * (8 - S));
   const unsigned long long M = (unsigned long long)n + bias;
   unsigned short *out = reinterpret_cast<unsigned short *>(dst);
@@ -74,6 +74,10 @@ __device__ __forceinline__ void write_fixed_slices(double x, int e, __nv_bfloat1
     const int j = S - 1 - s;  // byte of M that holds slice s
     out[s * plane] = bf16_bits_small((int)((M >> (8 * j)) & 255u) - 128);
   }
+}
+
+__device__ __forceinline__ void write_fixed_slices(double x, int e, __nv_bfloat16 *dst, long long plane, int S) {
+  write_int_slices(fixed_point(x, e, 7 + 8 * (S - 1)), dst, plane, S);
 }
 
 // The same digits as write_fixed_slices for a compile-time S, returned as BF16
@@ -90,6 +94,42 @@ __device__ __forceinline__ void fixed_digits(double x, int e, unsigned short (&d
   for (int s = 1; s < S; ++s) d[s] = bf16_bits_small((int)((M >> (8 * (S - 1 - s))) & 255u) - 128);
 }
 
+// round(x 2^(P - e)) for an FP32 x with |x| < 2^e (ties away from zero),
+// from the bits of x; P <= 31.
+__device__ __forceinline__ int fixed_point_f32(float x, int e, int P) {
+  const unsigned b = __float_as_uint(x);
+  const int E = (int)((b >> 23) & 0xFFu);
+  if (E == 0) return 0;
+  const unsigned mant = (b & 0x7FFFFFu) | 0x800000u;
+  const int sh = E - 150 + P - e;  // x = mant 2^(E-150)
+  int n;
+  if (sh >= 0) {
+    n = sh < 8 ? (int)(mant << sh) : 0;  // |x| < 2^e keeps this within P + 1 bits
+  } else {
+    const int r = -sh;
+    n = r > 25 ? 0 : (int)((mant + (1u << (r - 1))) >> r);
+  }
+  return (b >> 31) ? -n : n;
+}
+
+// The FP32 value nearest to x 2^k (ties away from zero) for a finite FP64 x,
+// from its bits (no FP64-pipe instruction); zero where the result would be
+// below FP32's normal range.  The caller keeps |x 2^k| below 2^127.
+__device__ __forceinline__ float double_to_scaled_float(double x, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return 0.0f;
+  unsigned long long m = ((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
+  m = (m + (1ULL << 28)) >> 29;  // 24 bits, or 2^24 after a carry
+  int e8 = E - 1023 + k + 127;
+  if (m >> 24) {
+    m >>= 1;
+    ++e8;
+  }
+  if (e8 <= 0) return 0.0f;
+  return __uint_as_float((unsigned)((b >> 63) << 31) | ((unsigned)e8 << 23) | ((unsigned)m & 0x7FFFFFu));
+}
+
 // The FP64 value of f * 2^k for a finite FP32 f, assembled from the bits of f
 // with integer operations (no FP64-pipe instruction).  Zero and FP32
 // subnormals (|f| < 2^-126, far below every value these kernels produce)
@@ -102,6 +142,16 @@ __device__ __forceinline__ double scaled_float_to_double(float f, int k) {
   const unsigned long long e11 = (unsigned long long)(int)(e8 + 896 + k);
   const unsigned long long m = (unsigned long long)(b & 0x7FFFFFu) << 29;
   return __longlong_as_double((long long)(sign | (e11 << 52) | m));
+}
+
+// f 2^k as an FP64 value for any k: zero below FP64's normal range, an
+// infinity above it; otherwise exact.
+__device__ __forceinline__ double scaled_float_to_double_any(float f, int k) {
+  const unsigned b = __float_as_uint(f);
+  const int e11 = (int)((b >> 23) & 0xFFu) + 896 + k;
+  if (((b >> 23) & 0xFFu) == 0 || e11 <= 0) return 0.0;
+  if (e11 >= 2047) return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) | 0x7FF0000000000000ULL));
+  return scaled_float_to_double(f, k);
 }
 
 // The FP64 value nearest to x * 2^k (ties away from zero) for |x| < 2^62,

@@ -78,12 +78,17 @@ def test_roofline_picks_the_dominant_kernel_and_its_peak():
     assert r["achieved"] == pytest.approx(2.0e14 / 0.5 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / peaks.get("bf16_tflops_sustained", 1700.0))
     assert r["launches_per_step"] == 5 and r["avg_launch_ms"] == pytest.approx(50.0)
-    # FP64 kernels against the DFMA peak at the sampled clock, everything else against the copy bandwidth
+    # FP64 kernels against the DFMA peak at the sampled clock (the panel of the FP64 modes), the
+    # FP32 panel of the tensor-core modes against the FFMA peak, everything else against the copy
+    # bandwidth
     named["tcx outer update"]["ms"] = 1.0
-    r = bench.roofline(None, named, steps, "mixed", sm_mhz=1900.0, sms=152)
+    r = bench.roofline(None, named, steps, "fp64emu", sm_mhz=1900.0, sms=152)
     assert r["kernel"] == "panel_kernel" and r["bound"] == "alu"
     assert r["peak"] == pytest.approx(152 * 4 * 1900e6 / 1e12)
     assert r["frac"] == pytest.approx(2.0e10 / 0.3 / 1e12 / r["peak"])
+    r = bench.roofline(None, named, steps, "mixed", sm_mhz=1900.0, sms=152)
+    assert r["kernel"] == "panel_kernel" and r["bound"] == "alu"
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * 1900e6 / 1e12)
     named["panel_kernel"]["ms"] = 1.0
     r = bench.roofline(None, named, steps, "mixed")
     assert r["kernel"] == "split_exact_kernel" and r["bound"] == "hbm" and r["unit"] == "GB/s"
