@@ -23,6 +23,7 @@
 // the factorization unique).
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "qr.cuh"
@@ -117,34 +118,62 @@ __device__ void larft_core(int bw, LarftSmem &L, const double *tau, double *T, b
 
 
 // Per-block partial Gram matrix of the rounded vectors, upper triangle column
-// by column (entry (a, j), a <= j, at j (j + 1) / 2 + a).
-__shared__ double g_gacc[QR_B * (QR_B + 1) / 2];
+// by column (entry (a, j), a <= j, at j (j + 1) / 2 + a): FP64 sums for the
+// FP64 panel, exact 64-bit integer sums for the FP32 one.
+__shared__ unsigned long long g_gacc[QR_B * (QR_B + 1) / 2];
+
+// V^ as the panel tail keeps it: FP64 values for the FP64 panel; for the FP32
+// panel the integers N = V^ 2^(P - vexp) (|N| <= 2^(P - vexp) (1 + 2^-23)).
+template <typename Real>
+using TailV = typename std::conditional<sizeof(Real) == 4, int, double>::type;
 
 // Column j of the tensor-core QR's panel is final: round it to the grid
 // 2^(vexp - P) into V^ (0 above the diagonal, 1 on it; Vh is the second copy
 // after Ps, or Ps itself) and add this block's rows to the Gram column (a, j),
-// a <= j.  Entries of V are at most 1 in magnitude, so with Real = float and
-// P = 31 (or less) every rounded entry is again a float: the grid is no finer
-// than a float's spacing wherever the float has bits below the grid.  The
-// products of two floats are exact in FP64; the sums are FP64.
-template <typename Real>
-__device__ void tail_column(int j, int ch, const Real *Ps, Real *Vh, int r0, int nr, const PanelTail &tl) {
+// a <= j.
+//
+// FP64 panel: FP64 products and sums.  FP32 panel: every entry of V is at most
+// 1 + 2^-23 in magnitude (|v_i| = |x_i| / |v0| with |v0| >= ||x||), so
+// ||v^||^2 <= 2 (1 + 2^-22) and, by Cauchy-Schwarz, every partial sum of
+// products of the integers N is below 2^(2(P - vexp) + 1) <= 2^61: the Gram
+// matrix of V^ is formed exactly in 64-bit integer arithmetic.
+__device__ void tail_column(int j, int cs, const double *Ps, double *Vh, int r0, int nr, const PanelTail &tl) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double unit = __longlong_as_double((long long)(1023 + tl.vexp - tl.P) << 52);  // 2^(vexp - P)
   for (int i = tid; i < nr; i += PNT) {
     const int gi = r0 + i;
-    Vh[j * ch + i] = gi < j ? Real(0) : (gi == j ? Real(1)
-                                                 : (Real)((double)fixed_point((double)Ps[j * ch + i], tl.vexp, tl.P) * unit));
+    Vh[j * cs + i] = gi < j ? 0.0 : (gi == j ? 1.0 : (double)fixed_point(Ps[j * cs + i], tl.vexp, tl.P) * unit);
   }
   __syncthreads();
-  const Real *xj = Vh + j * ch;
+  const double *xj = Vh + j * cs;
+  double *gacc = reinterpret_cast<double *>(g_gacc);
   for (int a = warp; a <= j; a += PW) {
-    const Real *xa = Vh + a * ch;
+    const double *xa = Vh + a * cs;
     double sum = 0.0;
-    for (int i = lane; i < nr; i += 32) sum = fma((double)xa[i], (double)xj[i], sum);
+    for (int i = lane; i < nr; i += 32) sum = fma(xa[i], xj[i], sum);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) g_gacc[j * (j + 1) / 2 + a] = sum;
+    if (lane == 0) gacc[j * (j + 1) / 2 + a] = sum;
+  }
+}
+
+__device__ void tail_column(int j, int cs, const float *Ps, int *Vh, int r0, int nr, const PanelTail &tl) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int one = 1 << (tl.P - tl.vexp);
+  for (int i = tid; i < nr; i += PNT) {
+    const int gi = r0 + i;
+    Vh[j * cs + i] = gi < j ? 0 : (gi == j ? one : fixed_point_f32(Ps[j * cs + i], tl.vexp, tl.P));
+  }
+  __syncthreads();
+  const int *xj = Vh + j * cs;
+  long long *gacc = reinterpret_cast<long long *>(g_gacc);
+  for (int a = warp; a <= j; a += PW) {
+    const int *xa = Vh + a * cs;
+    long long sum = 0;
+    for (int i = lane; i < nr; i += 32) sum += (long long)xa[i] * xj[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) gacc[j * (j + 1) / 2 + a] = sum;
   }
 }
 
@@ -153,18 +182,20 @@ __device__ void tail_column(int j, int ch, const Real *Ps, Real *Vh, int r0, int
 // rounded, with their Gram columns); F has been written.  `nbar` grid
 // barriers came before.
 template <typename Real>
-__device__ void panel_tail(int bw, int ch, Real *Ps, int c, int P, int r0, int nr, const double *tau,
+__device__ void panel_tail(int bw, int cs, Real *Ps, int c, int P, int r0, int nr, const double *tau,
                            unsigned *counter, DeviceControl *ctrl, const PanelTail &tl, unsigned nbar) {
+  using V = TailV<Real>;
+  constexpr bool EXACT = sizeof(Real) == 4;  // integer V^ and Gram matrix
   __shared__ LarftSmem L;
   __shared__ unsigned char pa[QR_B * (QR_B + 1) / 2], pb[QR_B * (QR_B + 1) / 2];
-  Real *Vh = tl.overlap ? Ps + (size_t)ch * QR_B : Ps;
-  int *es = reinterpret_cast<int *>(Vh + (size_t)ch * QR_B);  // ch row exponents after V^
+  V *Vh = tl.overlap ? reinterpret_cast<V *>(Ps + (size_t)cs * QR_B) : reinterpret_cast<V *>(Ps);
+  int *es = reinterpret_cast<int *>(Vh + (size_t)cs * QR_B);  // the slab's row exponents after V^
   const int tid = threadIdx.x;
   const int npairs = bw * (bw + 1) / 2;
   __syncthreads();
   // (1) the last column (every column when V^ is rounded in place)
   for (int j = tl.overlap ? bw - 1 : 0; j < bw; ++j) {
-    tail_column(j, ch, Ps, Vh, r0, nr, tl);
+    tail_column(j, cs, Ps, Vh, r0, nr, tl);
     __syncthreads();
   }
   for (int idx = tid; idx < npairs; idx += PNT) {  // upper-triangle pair table (a <= b), column by column
@@ -174,39 +205,61 @@ __device__ void panel_tail(int bw, int ch, Real *Ps, int c, int P, int r0, int n
     pb[idx] = (unsigned char)b;
   }
   __syncthreads();
-  // (2) natural slices, exponent vexp per column; (3) row exponents
+  // (2) natural slices, exponent vexp per column (for the integers N these
+  // are N's own digits); (3) row exponents
   for (int e = tid; e < nr * bw; e += PNT) {
     const int i = e % nr, t = e / nr;
-    write_fixed_slices((double)Vh[t * ch + i], tl.vexp, tl.vs.base + (r0 + i) + (long long)t * tl.vs.ld,
-                       tl.vs.plane, tl.vs.S);
+    __nv_bfloat16 *dst = tl.vs.base + (r0 + i) + (long long)t * tl.vs.ld;
+    if constexpr (EXACT) write_int_slices(Vh[t * cs + i], dst, tl.vs.plane, tl.vs.S);
+    else write_fixed_slices(Vh[t * cs + i], tl.vexp, dst, tl.vs.plane, tl.vs.S);
   }
   if (c == 0 && tid < bw) tl.vs.scale[tid] = tl.vexp;
   for (int i = tid; i < nr; i += PNT) {
-    unsigned long long mx = 0;
-    for (int t = 0; t < bw; ++t) mx = max(mx, abs_bits((double)Vh[t * ch + i]));
-    es[i] = exp_above_bits(mx);
+    if constexpr (EXACT) {
+      // |V^| < 2^e for e = msb(max |N|) + 1 + vexp - P (0 for a zero row)
+      unsigned mx = 0;
+      for (int t = 0; t < bw; ++t) mx = max(mx, (unsigned)abs(Vh[t * cs + i]));
+      es[i] = mx == 0 ? 0 : (32 - __clz((int)mx)) + tl.vexp - tl.P;
+    } else {
+      unsigned long long mx = 0;
+      for (int t = 0; t < bw; ++t) mx = max(mx, abs_bits(Vh[t * cs + i]));
+      es[i] = exp_above_bits(mx);
+    }
     tl.vts.scale[r0 + i] = es[i];
   }
   __syncthreads();
-  // transposed slices, the lanes along the columns
+  // transposed slices, the lanes along the columns (for the integers N:
+  // N 2^(vexp - e) exactly, e <= vexp)
   for (int e = tid; e < nr * bw; e += PNT) {
     const int t = e % bw, i = e / bw;
-    write_fixed_slices((double)Vh[t * ch + i], es[i], tl.vts.base + t + (long long)(r0 + i) * tl.vts.ld,
-                       tl.vts.plane, tl.vts.S);
+    __nv_bfloat16 *dst = tl.vts.base + t + (long long)(r0 + i) * tl.vts.ld;
+    if constexpr (EXACT) write_int_slices((long long)Vh[t * cs + i] * (1LL << (tl.vexp - es[i])), dst, tl.vts.plane, tl.vts.S);
+    else write_fixed_slices(Vh[t * cs + i], es[i], dst, tl.vts.plane, tl.vts.S);
   }
   // (4) this block's part of the Gram matrix (formed column by column)
-  for (int idx = tid; idx < npairs; idx += PNT) __stcg(&tl.gpart[(size_t)c * npairs + idx], g_gacc[idx]);
+  for (int idx = tid; idx < npairs; idx += PNT)
+    __stcg(reinterpret_cast<unsigned long long *>(tl.gpart) + (size_t)c * npairs + idx, g_gacc[idx]);
   if (!grid_barrier(counter, (nbar + 1) * P, ctrl)) return;
   // (5) distributed sum over the blocks in a fixed order: warp w of block c
-  // takes entry c + P w
+  // takes entry c + P w (integer sums are exact, then scaled to V^'s unit
+  // squared and rounded once)
   {
     const int lane = tid & 31, warp = tid >> 5;
     for (int idx = c + P * warp; idx < npairs; idx += P * PW) {
-      double sum = 0.0;
-      for (int z = lane; z < P; z += 32) sum += __ldcg(&tl.gpart[(size_t)z * npairs + idx]);
+      if constexpr (EXACT) {
+        const long long *gp = reinterpret_cast<const long long *>(tl.gpart);
+        long long sum = 0;
+        for (int z = lane; z < P; z += 32) sum += __ldcg(&gp[(size_t)z * npairs + idx]);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      if (lane == 0) __stcg(&tl.G[idx], sum);
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) __stcg(&tl.G[idx], int64_scaled_to_double(sum, 2 * (tl.vexp - tl.P)));
+      } else {
+        double sum = 0.0;
+        for (int z = lane; z < P; z += 32) sum += __ldcg(&tl.gpart[(size_t)z * npairs + idx]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) __stcg(&tl.G[idx], sum);
+      }
     }
   }
   if (!grid_barrier(counter, (nbar + 2) * P, ctrl)) return;
@@ -250,16 +303,19 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
   constexpr bool SCALED = sizeof(Real) == 4;
   constexpr unsigned base = SCALED ? 1u : 0u;  // grid barriers before column 0
   extern __shared__ __align__(16) unsigned char p_smem[];
-  Real *Ps = reinterpret_cast<Real *>(p_smem);  // ch x QR_B, column-major (column t at Ps + t*ch)
+  Real *Ps = reinterpret_cast<Real *>(p_smem);  // the slab, column-major (column t at Ps + t*cs)
   __shared__ Real s_w[QR_B];
   __shared__ double s_par[4];     // beta, -, tau, 1/v0
+  __shared__ float s_parf[3];     // tau, 1/v0, beta in FP32 (FP32 panel)
   __shared__ double s_beta[QR_B];
-  __shared__ double s_up[QR_B];   // per-column factor back to F's scale (scaled panels)
+  __shared__ double s_up[QR_B];   // per-column factor back to F's scale (scaled panels) ...
+  __shared__ int s_ke[QR_B];      // ... and its exponent
   __shared__ Real s_red[PW][32];
   const int P = gridDim.x;
   const int c = blockIdx.x;
   const int r0 = c * ch;
   const int nr = max(0, min(rows, r0 + ch) - r0);
+  const int cs = ch | 1;  // column stride of Ps: odd, so a warp reading one row across columns hits distinct banks
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   Real *parts = reinterpret_cast<Real *>(part);
   Real *rows_k = reinterpret_cast<Real *>(rowk);
@@ -296,16 +352,17 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
       for (int j = 0; j < PW; ++j) E = max(E, s_ex[j][tid]);
       s_up[tid] = ldexp(1.0, E - 1023);  // largest entry / 2^(E-1023) lies in [1, 2)
       s_ex[0][tid] = E;
+      s_ke[tid] = E - 1023;
     }
     __syncthreads();
     for (int e = tid; e < ch * bw; e += PNT) {
       const int i = e % ch, t = e / ch;
-      Ps[t * ch + i] = (i < nr) ? (Real)ldexp(F[(r0 + i) + t * ldf], 1023 - s_ex[0][t]) : Real(0);
+      Ps[t * cs + i] = (i < nr) ? double_to_scaled_float(F[(r0 + i) + t * ldf], 1023 - s_ex[0][t]) : Real(0);
     }
   } else {
     for (int e = tid; e < ch * bw; e += PNT) {
       const int i = e % ch, t = e / ch;
-      Ps[t * ch + i] = (i < nr) ? (Real)F[(r0 + i) + t * ldf] : Real(0);
+      Ps[t * cs + i] = (i < nr) ? (Real)F[(r0 + i) + t * ldf] : Real(0);
     }
   }
   __syncthreads();
@@ -316,24 +373,43 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
     Real *rk = rows_k + (size_t)buf * QR_B;
     // rows of this block strictly below row k
     const int i_lo = max(0, k + 1 - r0);
-    // (a) partials: t == k gives sum x_i^2, t > k gives sum x_i a_it
-    for (int t = k + warp; t < bw; t += PW) {
-      Real s = 0;
-      for (int i = i_lo + lane; i < nr; i += 32) s += Ps[k * ch + i] * Ps[t * ch + i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) __stcg(&pb[(size_t)c * QR_B + t], s);
+    // (a) partials: t == k gives sum x_i^2, t > k gives sum x_i a_it.  Thread
+    // (t = lane, g = warp) sums rows i_lo + g, i_lo + g + 8, ... (the odd
+    // column stride keeps the lanes' reads of one row on distinct banks); warp 0
+    // adds the 8 row groups in a fixed order and publishes the block's
+    // partials and, in the block holding it, row k.
+    {
+      Real s0 = 0, s1 = 0;
+      if (lane >= k && lane < bw) {
+        int i = i_lo + warp;
+        for (; i + PW < nr; i += 2 * PW) {
+          s0 += Ps[k * cs + i] * Ps[lane * cs + i];
+          s1 += Ps[k * cs + i + PW] * Ps[lane * cs + i + PW];
+        }
+        if (i < nr) s0 += Ps[k * cs + i] * Ps[lane * cs + i];
+      }
+      s_red[warp][lane] = s0 + s1;
     }
-    if (k >= r0 && k < r0 + nr)
-      for (int t = k + tid; t < bw; t += PNT) __stcg(&rk[t], Ps[t * ch + (k - r0)]);
-    // (b) one barrier per column.  The tensor-core QR's panel rounds the
-    // previous column's vector and forms its Gram column between arriving and
-    // waiting (the FP64 pipe is otherwise idle there).
+    __syncthreads();
+    if (warp == 0) {
+      Real S = 0;
+#pragma unroll
+      for (int j = 0; j < PW; ++j) S += s_red[j][lane];
+      if (lane >= k && lane < bw) {
+        __stcg(&pb[(size_t)c * QR_B + lane], S);
+        if (k >= r0 && k < r0 + nr) __stcg(&rk[lane], Ps[lane * cs + (k - r0)]);
+      }
+    }
+    // (b) one barrier per column, arrived at by warp 0's thread 0 once the
+    // warp's stores are ordered before it.  The tensor-core QR's panel rounds
+    // the previous column's vector and forms its Gram column between arriving
+    // and waiting.
     const unsigned target = (unsigned)(k + 1 + base) * P;
     if constexpr (TAIL) {
-      __syncthreads();
+      __syncwarp();
       grid_arrive(counter);
-      if (tail.overlap && k > 0) tail_column(k - 1, ch, Ps, Ps + (size_t)ch * QR_B, r0, nr, tail);
+      if (tail.overlap && k > 0)
+        tail_column(k - 1, cs, Ps, reinterpret_cast<TailV<Real> *>(Ps + (size_t)cs * QR_B), r0, nr, tail);
       if (!grid_wait(counter, target, ctrl)) return;
     } else {
       if (!grid_barrier(counter, target, ctrl)) return;
@@ -365,46 +441,58 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
       Real S = 0;
 #pragma unroll
       for (int j = 0; j < PW; ++j) S += s_red[j][lane];  // S(k) = sigma, S(t>k) = dot_t
-      // the reflector's parameters in FP64
-      const double sigma = (double)__shfl_sync(0xffffffffu, S, k);
-      const double x0 = (double)__shfl_sync(0xffffffffu, rkt, k);
-      double beta, tk, inv_v0;
-      if (sigma == 0.0) {
-        beta = x0; tk = 0.0; inv_v0 = 1.0;
-      } else {
-        // one division: r = 1 / (v0 norm) gives 1/v0 = norm r and
-        // tau = (beta - x0) / beta = |v0| / norm = |v0| v0 r
-        const double norm = sqrt(fma(x0, x0, sigma));
-        beta = (x0 >= 0.0) ? -norm : norm;
-        const double v0 = x0 - beta;
-        const double r = 1.0 / (v0 * norm);
-        inv_v0 = norm * r;
-        tk = fabs(v0) * v0 * r;
+      const Real Sk = __shfl_sync(0xffffffffu, S, k), xk = __shfl_sync(0xffffffffu, rkt, k);
+      // the reflector's parameters in FP64 (for the FP32 panel on one lane:
+      // this GPU's FP64 unit takes many clocks per warp instruction)
+      if (!SCALED || lane == 0) {
+        const double sigma = (double)Sk, x0 = (double)xk;
+        double beta, tk, inv_v0;
+        if (sigma == 0.0) {
+          beta = x0; tk = 0.0; inv_v0 = 1.0;
+        } else {
+          // one division: r = 1 / (v0 norm) gives 1/v0 = norm r and
+          // tau = (beta - x0) / beta = |v0| / norm = |v0| v0 r
+          const double norm = sqrt(fma(x0, x0, sigma));
+          beta = (x0 >= 0.0) ? -norm : norm;
+          const double v0 = x0 - beta;
+          const double r = 1.0 / (v0 * norm);
+          inv_v0 = norm * r;
+          tk = fabs(v0) * v0 * r;
+        }
+        if constexpr (SCALED) {
+          s_parf[0] = (float)tk;  // in [1, 2] or 0
+          s_parf[1] = (float)inv_v0;
+          s_parf[2] = (float)beta;
+        } else {
+          // w_t = tau (a_kt + v(k+1:)^T a_t) with v(k+1:) = x(k+1:)/v0
+          if (lane > k && lane < bw) s_w[lane] = (Real)(tk * ((double)rkt + (double)S * inv_v0));
+        }
+        if (lane == 0) {
+          s_par[0] = beta; s_par[2] = tk; s_par[3] = inv_v0;
+          s_beta[k] = beta;
+          if (c == 0) tau[k] = tk;
+        }
       }
-      // w_t = tau (a_kt + v(k+1:)^T a_t) with v(k+1:) = x(k+1:)/v0
-      if (lane > k && lane < bw) s_w[lane] = (Real)(tk * ((double)rkt + (double)S * inv_v0));
-      if (lane == 0) {
-        s_par[0] = beta; s_par[2] = tk; s_par[3] = inv_v0;
-        s_beta[k] = beta;
-        if (c == 0) tau[k] = tk;
+      if constexpr (SCALED) {  // w_t in FP32, like the updates it feeds
+        __syncwarp();
+        if (lane > k && lane < bw) s_w[lane] = (Real)(s_parf[0] * (rkt + S * s_parf[1]));
       }
     }
     __syncthreads();
-    const double tk = s_par[2];
-    if (tk != 0.0) {
-      const Real iv = (Real)s_par[3];
-      for (int i = i_lo + tid; i < nr; i += PNT) Ps[k * ch + i] *= iv;
-      __syncthreads();
-      if (k >= r0 && k < r0 + nr && tid == 0) Ps[k * ch + (k - r0)] = (Real)s_par[0];
-      const int ncol = bw - k - 1;
-      const int i_from = max(0, k - r0);  // include row k itself (v_k = 1)
-      const int span = nr - i_from;
-      if (ncol > 0 && span > 0) {
-        for (int e = tid; e < ncol * span; e += PNT) {
-          int t = k + 1 + e / span, i = i_from + e % span;
-          Real v = (r0 + i == k) ? Real(1) : Ps[k * ch + i];
-          Ps[t * ch + i] -= s_w[t] * v;
-        }
+    if (SCALED ? s_parf[0] != 0.0f : s_par[2] != 0.0) {
+      // (d) v = x / v0 below row k, 1 at row k (where beta goes), and
+      // a_t -= w_t v for t > k: thread (t = lane, g = warp) takes rows
+      // i_from + g, i_from + g + 8, ...; lane k writes column k
+      const Real iv = SCALED ? (Real)s_parf[1] : (Real)s_par[3];
+      const Real beta = SCALED ? (Real)s_parf[2] : (Real)s_par[0];
+      const Real w = (lane > k && lane < bw) ? s_w[lane] : Real(0);
+      for (int i = max(0, k - r0) + warp; i < nr; i += PW) {
+        const bool diag = r0 + i == k;
+        const Real x = Ps[k * cs + i];
+        const Real v = diag ? Real(1) : x * iv;
+        __syncwarp();
+        if (lane == k) Ps[k * cs + i] = diag ? beta : v;
+        else if (lane > k && lane < bw) Ps[lane * cs + i] -= w * v;
       }
     }
     __syncthreads();
@@ -413,15 +501,17 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
   for (int e = tid; e < nr * bw; e += PNT) {
     int i = e % nr, t = e / nr;
     int gi = r0 + i;
-    double x = (double)Ps[t * ch + i];
+    double x;
     if constexpr (SCALED) {  // R back to F's scale (beta from FP64); V is scale-free
-      if (gi == t) x = s_beta[t];
-      if (gi <= t) x *= s_up[t];
+      const float f = Ps[t * cs + i];
+      x = gi == t ? s_beta[t] * s_up[t] : (gi < t ? scaled_float_to_double_any(f, s_ke[t]) : scaled_float_to_double(f, 0));
+    } else {
+      x = Ps[t * cs + i];
     }
     F[gi + t * ldf] = x;
     if constexpr (!TAIL) Vb[gi + t * ldv] = (gi < t) ? 0.0 : (gi == t ? 1.0 : x);
   }
-  if constexpr (TAIL) panel_tail(bw, ch, Ps, c, P, r0, nr, tau, counter, ctrl, tail, (unsigned)bw + base);
+  if constexpr (TAIL) panel_tail(bw, cs, Ps, c, P, r0, nr, tau, counter, ctrl, tail, (unsigned)bw + base);
 }
 
 // ------------------------------------------------------------ T factor ----
@@ -650,7 +740,7 @@ int panel_factor(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *
   if (!di) return PURL_ERR_CUDA;
   int P = panel_blocks(rows, di);
   int ch = ceil_div(rows, P);
-  size_t smem = (size_t)ch * QR_B * sizeof(double);
+  size_t smem = (size_t)(ch | 1) * QR_B * sizeof(double);
   int cap = panel_capacity<false, double>(di, smem);
   if (cap < P) return PURL_ERR_UNSUPPORTED;
   int ldv = rows;
@@ -673,10 +763,11 @@ static int panel_tail_launch(int rows, int bw, double *Fp, int ldf, double *taup
   // place at the end and its Gram columns formed there
   PanelTail tl = tail;
   const size_t es_bytes = align_up((size_t)ch * sizeof(int), 16);
-  size_t smem = 2 * (size_t)ch * QR_B * sizeof(Real) + es_bytes;
+  const size_t cs = (size_t)(ch | 1);  // the kernel's column stride
+  size_t smem = 2 * cs * QR_B * sizeof(Real) + es_bytes;
   tl.overlap = 1;
   if (panel_capacity<true, Real>(di, smem) < P) {
-    smem = (size_t)ch * QR_B * sizeof(Real) + es_bytes;
+    smem = cs * QR_B * sizeof(Real) + es_bytes;
     tl.overlap = 0;
   }
   int cap = panel_capacity<true, Real>(di, smem);
