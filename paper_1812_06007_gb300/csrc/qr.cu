@@ -44,6 +44,18 @@ constexpr int PNT = 256;  // panel kernel threads
 constexpr int PW = PNT / 32;
 constexpr int kPanelMaxBlocks = 160;  // panel grids have at most this many blocks (>= the SM count)
 
+// The FP32 panel's partial sums carry an epoch next to the value (one 64-bit
+// word), so a block waits for the data itself instead of for a barrier
+// counter: column k of the panel launch with epoch base e0 writes epoch e0 + k.
+// The QR zeroes the tagged buffers before its first panel and gives panel p
+// the base 1 + 32 p, so no word left by an earlier panel carries the current
+// epoch.
+__device__ __forceinline__ unsigned long long epoch_tag(unsigned ep, float v) {
+  return ((unsigned long long)ep << 32) | __float_as_uint(v);
+}
+__device__ __forceinline__ unsigned tag_epoch(unsigned long long w) { return (unsigned)(w >> 32); }
+__device__ __forceinline__ float tag_value(unsigned long long w) { return __uint_as_float((unsigned)w); }
+
 // ------------------------------------------------------------ panel tail --
 // Shared-memory work arrays of larft_core.
 struct LarftSmem {
@@ -117,94 +129,82 @@ __device__ void larft_core(int bw, LarftSmem &L, const double *tau, double *T, b
 }
 
 
-// Per-block partial Gram matrix of the rounded vectors, upper triangle column
-// by column (entry (a, j), a <= j, at j (j + 1) / 2 + a): FP64 sums for the
-// FP64 panel, exact 64-bit integer sums for the FP32 one.
-__shared__ unsigned long long g_gacc[QR_B * (QR_B + 1) / 2];
-
-// V^ as the panel tail keeps it: FP64 values for the FP64 panel; for the FP32
-// panel the integers N = V^ 2^(P - vexp) (|N| <= 2^(P - vexp) (1 + 2^-23)).
+// V^ as the panel tail keeps it, in place of the factored panel: FP64 values
+// for the FP64 panel; for the FP32 panel the integers N = V^ 2^(P - vexp)
+// (|N| <= 2^(P - vexp) (1 + 2^-23)).
 template <typename Real>
 using TailV = typename std::conditional<sizeof(Real) == 4, int, double>::type;
 
-// Column j of the tensor-core QR's panel is final: round it to the grid
-// 2^(vexp - P) into V^ (0 above the diagonal, 1 on it; Vh is the second copy
-// after Ps, or Ps itself) and add this block's rows to the Gram column (a, j),
-// a <= j.
-//
-// FP64 panel: FP64 products and sums.  FP32 panel: every entry of V is at most
-// 1 + 2^-23 in magnitude (|v_i| = |x_i| / |v0| with |v0| >= ||x||), so
-// ||v^||^2 <= 2 (1 + 2^-22) and, by Cauchy-Schwarz, every partial sum of
-// products of the integers N is below 2^(2(P - vexp) + 1) <= 2^61: the Gram
-// matrix of V^ is formed exactly in 64-bit integer arithmetic.
-__device__ void tail_column(int j, int cs, const double *Ps, double *Vh, int r0, int nr, const PanelTail &tl) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// Entry i of column j of the factored panel, rounded to the grid 2^(vexp - P):
+// 0 above the diagonal, 1 on it.
+__device__ __forceinline__ double round_entry(double x, int gi, int j, const PanelTail &tl) {
   const double unit = __longlong_as_double((long long)(1023 + tl.vexp - tl.P) << 52);  // 2^(vexp - P)
-  for (int i = tid; i < nr; i += PNT) {
-    const int gi = r0 + i;
-    Vh[j * cs + i] = gi < j ? 0.0 : (gi == j ? 1.0 : (double)fixed_point(Ps[j * cs + i], tl.vexp, tl.P) * unit);
-  }
-  __syncthreads();
-  const double *xj = Vh + j * cs;
-  double *gacc = reinterpret_cast<double *>(g_gacc);
-  for (int a = warp; a <= j; a += PW) {
-    const double *xa = Vh + a * cs;
-    double sum = 0.0;
-    for (int i = lane; i < nr; i += 32) sum = fma(xa[i], xj[i], sum);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) gacc[j * (j + 1) / 2 + a] = sum;
-  }
+  return gi < j ? 0.0 : (gi == j ? 1.0 : (double)fixed_point(x, tl.vexp, tl.P) * unit);
+}
+__device__ __forceinline__ int round_entry(float x, int gi, int j, const PanelTail &tl) {
+  return gi < j ? 0 : (gi == j ? 1 << (tl.P - tl.vexp) : fixed_point_f32(x, tl.vexp, tl.P));
 }
 
-__device__ void tail_column(int j, int cs, const float *Ps, int *Vh, int r0, int nr, const PanelTail &tl) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int one = 1 << (tl.P - tl.vexp);
-  for (int i = tid; i < nr; i += PNT) {
-    const int gi = r0 + i;
-    Vh[j * cs + i] = gi < j ? 0 : (gi == j ? one : fixed_point_f32(Ps[j * cs + i], tl.vexp, tl.P));
+// Gram entry sum_i a_i b_i over the block's rows: FP64 for the FP64 panel.
+// For the FP32 panel every entry of V is at most 1 + 2^-23 in magnitude
+// (|v_i| = |x_i| / |v0| with |v0| >= ||x||), so ||v^||^2 <= 2 (1 + 2^-22) and,
+// by Cauchy-Schwarz, every partial sum of products of the integers N is below
+// 2^(2(P - vexp) + 1) <= 2^61: the Gram matrix of V^ is exact in 64-bit
+// integers.
+__device__ __forceinline__ double gram_entry(const double *a, const double *b, int nr) {
+  double s0 = 0.0, s1 = 0.0;
+  int i = 0;
+  for (; i + 1 < nr; i += 2) {
+    s0 = fma(a[i], b[i], s0);
+    s1 = fma(a[i + 1], b[i + 1], s1);
   }
-  __syncthreads();
-  const int *xj = Vh + j * cs;
-  long long *gacc = reinterpret_cast<long long *>(g_gacc);
-  for (int a = warp; a <= j; a += PW) {
-    const int *xa = Vh + a * cs;
-    long long sum = 0;
-    for (int i = lane; i < nr; i += 32) sum += (long long)xa[i] * xj[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) gacc[j * (j + 1) / 2 + a] = sum;
+  if (i < nr) s0 = fma(a[i], b[i], s0);
+  return s0 + s1;
+}
+__device__ __forceinline__ long long gram_entry(const int *a, const int *b, int nr) {
+  long long s0 = 0, s1 = 0;
+  int i = 0;
+  for (; i + 1 < nr; i += 2) {
+    s0 += (long long)a[i] * b[i];
+    s1 += (long long)a[i + 1] * b[i + 1];
   }
+  if (i < nr) s0 += (long long)a[i] * b[i];
+  return s0 + s1;
 }
 
 // Slices, Gram matrix and T of a finished panel (see panel_kernel).  Ps holds
-// the block's rows of the factored panel, then V^ (columns 0..bw-2 already
-// rounded, with their Gram columns); F has been written.  `nbar` grid
-// barriers came before.
+// the block's rows of the factored panel (F has been written): below the
+// diagonal V itself, or for the FP32 panel x with V = x viv[column]; V^
+// replaces them.  `nbar` grid barriers came before.
 template <typename Real>
-__device__ void panel_tail(int bw, int cs, Real *Ps, int c, int P, int r0, int nr, const double *tau,
+__device__ void panel_tail(int bw, int cs, Real *Ps, const float *viv, int c, int P, int r0, int nr, const double *tau,
                            unsigned *counter, DeviceControl *ctrl, const PanelTail &tl, unsigned nbar) {
   using V = TailV<Real>;
   constexpr bool EXACT = sizeof(Real) == 4;  // integer V^ and Gram matrix
   __shared__ LarftSmem L;
   __shared__ unsigned char pa[QR_B * (QR_B + 1) / 2], pb[QR_B * (QR_B + 1) / 2];
-  V *Vh = tl.overlap ? reinterpret_cast<V *>(Ps + (size_t)cs * QR_B) : reinterpret_cast<V *>(Ps);
+  V *Vh = reinterpret_cast<V *>(Ps);
   int *es = reinterpret_cast<int *>(Vh + (size_t)cs * QR_B);  // the slab's row exponents after V^
   const int tid = threadIdx.x;
   const int npairs = bw * (bw + 1) / 2;
   __syncthreads();
-  // (1) the last column (every column when V^ is rounded in place)
-  for (int j = tl.overlap ? bw - 1 : 0; j < bw; ++j) {
-    tail_column(j, cs, Ps, Vh, r0, nr, tl);
-    __syncthreads();
+  // (1) V^ in place; the upper-triangle pair table (a <= b), column by column
+  for (int e = tid; e < nr * bw; e += PNT) {
+    const int i = e % nr, t = e / nr;
+    Vh[t * cs + i] = round_entry(viv ? (Real)(Ps[t * cs + i] * viv[t]) : Ps[t * cs + i], r0 + i, t, tl);
   }
-  for (int idx = tid; idx < npairs; idx += PNT) {  // upper-triangle pair table (a <= b), column by column
+  for (int idx = tid; idx < npairs; idx += PNT) {
     int b = 0, rem = idx;
     while (rem > b) { rem -= b + 1; ++b; }
     pa[idx] = (unsigned char)rem;
     pb[idx] = (unsigned char)b;
   }
   __syncthreads();
+  // this block's part of the Gram matrix, one thread per entry
+  for (int idx = tid; idx < npairs; idx += PNT) {
+    auto g = gram_entry(Vh + pa[idx] * cs, Vh + pb[idx] * cs, nr);
+    __stcg(reinterpret_cast<decltype(g) *>(tl.gpart) + (size_t)c * npairs + idx, g);
+  }
   // (2) natural slices, exponent vexp per column (for the integers N these
   // are N's own digits); (3) row exponents
   for (int e = tid; e < nr * bw; e += PNT) {
@@ -236,9 +236,6 @@ __device__ void panel_tail(int bw, int cs, Real *Ps, int c, int P, int r0, int n
     if constexpr (EXACT) write_int_slices((long long)Vh[t * cs + i] * (1LL << (tl.vexp - es[i])), dst, tl.vts.plane, tl.vts.S);
     else write_fixed_slices(Vh[t * cs + i], es[i], dst, tl.vts.plane, tl.vts.S);
   }
-  // (4) this block's part of the Gram matrix (formed column by column)
-  for (int idx = tid; idx < npairs; idx += PNT)
-    __stcg(reinterpret_cast<unsigned long long *>(tl.gpart) + (size_t)c * npairs + idx, g_gacc[idx]);
   if (!grid_barrier(counter, (nbar + 1) * P, ctrl)) return;
   // (5) distributed sum over the blocks in a fixed order: warp w of block c
   // takes entry c + P w (integer sums are exact, then scaled to V^'s unit
@@ -276,6 +273,20 @@ __device__ void panel_tail(int bw, int cs, Real *Ps, int c, int P, int r0, int n
   larft_core(bw, L, tau, tl.T, true);
 }
 
+// FP32 panel: beta = -sign(x0) ||x|| (R(j,j)) and tau = |v0| / ||x|| of column j
+// in FP64 from the FP32 sums sigma and x0 it was formed from.
+__device__ __forceinline__ void panel_beta_tau(int j, const float2 *sx, double *s_beta, double *tau) {
+  const double sigma = sx[j].x, x0 = sx[j].y;
+  double beta = x0, tk = 0.0;
+  if (sigma != 0.0) {
+    const double norm = sqrt(fma(x0, x0, sigma));
+    beta = x0 >= 0.0 ? -norm : norm;
+    tk = (fabs(x0) + norm) / norm;
+  }
+  s_beta[j] = beta;
+  if (tau) tau[j] = tk;
+}
+
 // ------------------------------------------------------------ panel -------
 // F points at F(j0, j0); the panel has `rows` rows and `bw` <= QR_B columns.
 // Block c owns panel rows [c*ch, min(rows, (c+1)*ch)).
@@ -306,7 +317,9 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
   Real *Ps = reinterpret_cast<Real *>(p_smem);  // the slab, column-major (column t at Ps + t*cs)
   __shared__ Real s_w[QR_B];
   __shared__ double s_par[4];     // beta, -, tau, 1/v0
-  __shared__ float s_parf[3];     // tau, 1/v0, beta in FP32 (FP32 panel)
+  __shared__ float s_parf[2];     // FP32 panel: tau, 1/v0 of the current column
+  __shared__ float s_iv[QR_B];    // FP32 panel: 1/v0 per column (V = x / v0 below the diagonal)
+  __shared__ float2 s_sx[QR_B];   // FP32 panel: sigma and x0 per column
   __shared__ double s_beta[QR_B];
   __shared__ double s_up[QR_B];   // per-column factor back to F's scale (scaled panels) ...
   __shared__ int s_ke[QR_B];      // ... and its exponent
@@ -319,11 +332,13 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   Real *parts = reinterpret_cast<Real *>(part);
   Real *rows_k = reinterpret_cast<Real *>(rowk);
+  unsigned long long *tparts = reinterpret_cast<unsigned long long *>(part);  // FP32 panel: tagged partials
+  unsigned long long *trows = reinterpret_cast<unsigned long long *>(rowk);
 
   if constexpr (SCALED) {
     // (0) the largest exponent field of each column over all blocks
     __shared__ int s_ex[PW][32];
-    int *pe = reinterpret_cast<int *>(parts + (size_t)2 * P * QR_B);
+    int *pe = reinterpret_cast<int *>(part + (size_t)2 * P * QR_B);  // after the two tagged buffers
     for (int t = warp; t < bw; t += PW) {
       unsigned mx = 0;
       for (int i = lane; i < nr; i += 32)
@@ -391,40 +406,81 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
       s_red[warp][lane] = s0 + s1;
     }
     __syncthreads();
+    const unsigned ep = tail.epoch0 + (unsigned)k;
     if (warp == 0) {
       Real S = 0;
 #pragma unroll
       for (int j = 0; j < PW; ++j) S += s_red[j][lane];
       if (lane >= k && lane < bw) {
-        __stcg(&pb[(size_t)c * QR_B + lane], S);
-        if (k >= r0 && k < r0 + nr) __stcg(&rk[lane], Ps[lane * cs + (k - r0)]);
+        if constexpr (SCALED) {
+          __stcg(&tparts[(size_t)buf * P * QR_B + (size_t)c * QR_B + lane], epoch_tag(ep, S));
+          if (k >= r0 && k < r0 + nr) __stcg(&trows[buf * QR_B + lane], epoch_tag(ep, Ps[lane * cs + (k - r0)]));
+        } else {
+          __stcg(&pb[(size_t)c * QR_B + lane], S);
+          if (k >= r0 && k < r0 + nr) __stcg(&rk[lane], Ps[lane * cs + (k - r0)]);
+        }
       }
     }
-    // (b) one barrier per column, arrived at by warp 0's thread 0 once the
-    // warp's stores are ordered before it.  The tensor-core QR's panel rounds
-    // the previous column's vector and forms its Gram column between arriving
-    // and waiting.
-    const unsigned target = (unsigned)(k + 1 + base) * P;
-    if constexpr (TAIL) {
-      __syncwarp();
-      grid_arrive(counter);
-      if (tail.overlap && k > 0)
-        tail_column(k - 1, cs, Ps, reinterpret_cast<TailV<Real> *>(Ps + (size_t)cs * QR_B), r0, nr, tail);
-      if (!grid_wait(counter, target, ctrl)) return;
-    } else {
-      if (!grid_barrier(counter, target, ctrl)) return;
+    // (b) FP64 panel: one barrier per column, arrived at by warp 0's thread 0
+    // once the warp's stores are ordered before it.  FP32 panel: no barrier;
+    // (c) waits for the tagged partials themselves.
+    if constexpr (!SCALED) {
+      if (!grid_barrier(counter, (unsigned)(k + 1 + base) * P, ctrl)) return;
     }
-    // (c) every block reduces the partials in the same fixed order: thread
-    // (t = tid % 32, j = tid / 32) sums blocks j, j + 8, ... with independent
-    // loads (one L2 round trip, not one per block), warp 0 adds the 8 partial
-    // sums and forms the reflector.  Row k is fetched in the same round trip.
-    const Real rkt = (warp == 0 && lane < bw) ? __ldcg(&rk[lane]) : Real(0);
-    {
+    // (c) every block reduces the partials in the same fixed order; warp 0 adds
+    // the 8 partial sums and forms the reflector.
+    Real rkt = 0;
+    if constexpr (SCALED) {
+      // thread (t = lane, j = warp) loads the tagged partials of blocks j,
+      // j + 8, ... (and warp 0 row k) and reloads those not yet of epoch ep
+      // (bounded, as the grid barrier), then adds them in a fixed order
+      const int t = lane, j = warp;
+      const unsigned long long *tp = tparts + (size_t)buf * P * QR_B + t;
+      Real acc = 0;
+      bool fail = false;
+      if (t >= k && t < bw) {
+        unsigned long long v[kPanelMaxBlocks / PW];
+        unsigned long long r = warp == 0 ? __ldcg(&trows[buf * QR_B + t]) : epoch_tag(ep, 0.0f);
+#pragma unroll
+        for (int u = 0; u < kPanelMaxBlocks / PW; ++u) {
+          const int b = j + u * PW;
+          v[u] = (b < P) ? __ldcg(tp + (size_t)b * QR_B) : epoch_tag(ep, 0.0f);
+        }
+        long long polls = 0;
+        while (true) {
+          bool all = tag_epoch(r) == ep;
+#pragma unroll
+          for (int u = 0; u < kPanelMaxBlocks / PW; ++u) all &= tag_epoch(v[u]) == ep;
+          if (all) break;
+          if ((++polls & 63) == 0 && *(volatile int *)&ctrl->abort) { fail = true; break; }
+          if (polls > kSpinLimit) {
+            atomicCAS(&ctrl->status, PURL_OK, PURL_ERR_TIMEOUT);
+            atomicExch(&ctrl->abort, 1);
+            fail = true;
+            break;
+          }
+          if (tag_epoch(r) != ep) r = __ldcg(&trows[buf * QR_B + t]);
+#pragma unroll
+          for (int u = 0; u < kPanelMaxBlocks / PW; ++u)
+            if (tag_epoch(v[u]) != ep) v[u] = __ldcg(tp + (size_t)(j + u * PW) * QR_B);
+        }
+#pragma unroll
+        for (int u = 0; u < kPanelMaxBlocks / PW; ++u) acc += tag_value(v[u]);
+        rkt = tag_value(r);
+      }
+      // thread 0 (t = 0 < k, no partials to wait for) forms the previous
+      // column's beta and tau in FP64 meanwhile
+      if (tid == 0 && k > 0) panel_beta_tau(k - 1, s_sx, s_beta, c == 0 ? tau : nullptr);
+      s_red[j][t] = acc;
+      if (__syncthreads_or(fail)) return;
+    } else {
+      // every block reduces the partials in the same fixed order: thread
+      // (t = tid % 32, j = tid / 32) sums blocks j, j + 8, ... with independent
+      // loads (one L2 round trip, not one per block); row k comes in the same trip
+      rkt = (warp == 0 && lane < bw) ? __ldcg(&rk[lane]) : Real(0);
       const int t = tid & 31, j = tid >> 5;
       Real acc = 0;
       if (t >= k && t < bw) {
-        // all of this thread's partials are loaded before any is added, so
-        // the loads share one round trip (P <= kPanelMaxBlocks)
         Real v[kPanelMaxBlocks / PW];
 #pragma unroll
         for (int u = 0; u < kPanelMaxBlocks / PW; ++u) {
@@ -435,17 +491,56 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
         for (int u = 0; u < kPanelMaxBlocks / PW; ++u) acc += v[u];
       }
       s_red[j][t] = acc;
+      __syncthreads();
     }
-    __syncthreads();
-    if (warp == 0) {
-      Real S = 0;
+    if constexpr (SCALED) {
+      // FP32 panel: the reflector in FP32, by every lane of warp 0 (its inputs
+      // are FP32 sums): two independent chains, 1/||x|| and 1/sigma; with
+      // |v0| = |x0| + ||x||, tau = |v0| / ||x|| and 1/|v0| = (||x|| - |x0|) / sigma
+      // (no cancellation while sigma >= x0^2; otherwise 1/|v0| directly).
+      // beta (for R(k,k)) and tau follow in FP64 off the critical path.
+      if (warp == 0) {
+        Real S = 0;
 #pragma unroll
-      for (int j = 0; j < PW; ++j) S += s_red[j][lane];  // S(k) = sigma, S(t>k) = dot_t
-      const Real Sk = __shfl_sync(0xffffffffu, S, k), xk = __shfl_sync(0xffffffffu, rkt, k);
-      // the reflector's parameters in FP64 (for the FP32 panel on one lane:
-      // this GPU's FP64 unit takes many clocks per warp instruction)
-      if (!SCALED || lane == 0) {
-        const double sigma = (double)Sk, x0 = (double)xk;
+        for (int j = 0; j < PW; ++j) S += s_red[j][lane];  // S(k) = sigma, S(t>k) = dot_t
+        const float sigma = __shfl_sync(0xffffffffu, S, k), x0 = __shfl_sync(0xffffffffu, rkt, k);
+        float tk = 0.0f, iv = 1.0f;
+        if (sigma != 0.0f) {
+          const float n2 = fmaf(x0, x0, sigma), ax = fabsf(x0);
+          const float rn = rsqrtf(n2), rs = __frcp_rn(sigma);
+          const float norm = n2 * rn;
+          const float iav0 = sigma >= x0 * x0 ? (norm - ax) * rs : __frcp_rn(ax + norm);
+          tk = (ax + norm) * rn;
+          iv = x0 >= 0.0f ? iav0 : -iav0;
+        }
+        // w_t = tau (a_kt + v(k+1:)^T a_t) with v(k+1:) = x(k+1:)/v0
+        if (lane > k && lane < bw) s_w[lane] = tk * (rkt + S * iv);
+        if (lane == 0) {
+          s_parf[0] = tk;
+          s_parf[1] = iv;
+          s_iv[k] = iv;
+          s_sx[k] = make_float2(sigma, x0);
+        }
+      }
+      __syncthreads();
+      if (s_parf[0] != 0.0f) {
+        // (d) a_t -= w_t v for t > k, v = x / v0 below row k and 1 at row k:
+        // thread (t = lane, g = warp) takes rows i_from + g, i_from + g + 8, ...
+        // Column k itself stays unscaled (v is formed where it is used).
+        const Real iv = s_parf[1];
+        const Real w = (lane > k && lane < bw) ? s_w[lane] : Real(0);
+        for (int i = max(0, k - r0) + warp; i < nr; i += PW) {
+          const Real v = (r0 + i == k) ? Real(1) : Ps[k * cs + i] * iv;
+          if (lane > k && lane < bw) Ps[lane * cs + i] -= w * v;
+        }
+      }
+      __syncthreads();
+    } else {
+      if (warp == 0) {
+        Real S = 0;
+#pragma unroll
+        for (int j = 0; j < PW; ++j) S += s_red[j][lane];  // S(k) = sigma, S(t>k) = dot_t
+        const double sigma = (double)__shfl_sync(0xffffffffu, S, k), x0 = (double)__shfl_sync(0xffffffffu, rkt, k);
         double beta, tk, inv_v0;
         if (sigma == 0.0) {
           beta = x0; tk = 0.0; inv_v0 = 1.0;
@@ -459,42 +554,35 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
           inv_v0 = norm * r;
           tk = fabs(v0) * v0 * r;
         }
-        if constexpr (SCALED) {
-          s_parf[0] = (float)tk;  // in [1, 2] or 0
-          s_parf[1] = (float)inv_v0;
-          s_parf[2] = (float)beta;
-        } else {
-          // w_t = tau (a_kt + v(k+1:)^T a_t) with v(k+1:) = x(k+1:)/v0
-          if (lane > k && lane < bw) s_w[lane] = (Real)(tk * ((double)rkt + (double)S * inv_v0));
-        }
+        // w_t = tau (a_kt + v(k+1:)^T a_t) with v(k+1:) = x(k+1:)/v0
+        if (lane > k && lane < bw) s_w[lane] = (Real)(tk * ((double)rkt + (double)S * inv_v0));
         if (lane == 0) {
           s_par[0] = beta; s_par[2] = tk; s_par[3] = inv_v0;
-          s_beta[k] = beta;
           if (c == 0) tau[k] = tk;
         }
       }
-      if constexpr (SCALED) {  // w_t in FP32, like the updates it feeds
-        __syncwarp();
-        if (lane > k && lane < bw) s_w[lane] = (Real)(s_parf[0] * (rkt + S * s_parf[1]));
+      __syncthreads();
+      if (s_par[2] != 0.0) {
+        // (d) v = x / v0 below row k, 1 at row k (where beta goes), and
+        // a_t -= w_t v for t > k: thread (t = lane, g = warp) takes rows
+        // i_from + g, i_from + g + 8, ...; lane k writes column k
+        const Real iv = (Real)s_par[3];
+        const Real beta = (Real)s_par[0];
+        const Real w = (lane > k && lane < bw) ? s_w[lane] : Real(0);
+        for (int i = max(0, k - r0) + warp; i < nr; i += PW) {
+          const bool diag = r0 + i == k;
+          const Real x = Ps[k * cs + i];
+          const Real v = diag ? Real(1) : x * iv;
+          __syncwarp();
+          if (lane == k) Ps[k * cs + i] = diag ? beta : v;
+          else if (lane > k && lane < bw) Ps[lane * cs + i] -= w * v;
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
-    if (SCALED ? s_parf[0] != 0.0f : s_par[2] != 0.0) {
-      // (d) v = x / v0 below row k, 1 at row k (where beta goes), and
-      // a_t -= w_t v for t > k: thread (t = lane, g = warp) takes rows
-      // i_from + g, i_from + g + 8, ...; lane k writes column k
-      const Real iv = SCALED ? (Real)s_parf[1] : (Real)s_par[3];
-      const Real beta = SCALED ? (Real)s_parf[2] : (Real)s_par[0];
-      const Real w = (lane > k && lane < bw) ? s_w[lane] : Real(0);
-      for (int i = max(0, k - r0) + warp; i < nr; i += PW) {
-        const bool diag = r0 + i == k;
-        const Real x = Ps[k * cs + i];
-        const Real v = diag ? Real(1) : x * iv;
-        __syncwarp();
-        if (lane == k) Ps[k * cs + i] = diag ? beta : v;
-        else if (lane > k && lane < bw) Ps[lane * cs + i] -= w * v;
-      }
-    }
+  }
+  if constexpr (SCALED) {
+    if (tid == 0) panel_beta_tau(bw - 1, s_sx, s_beta, c == 0 ? tau : nullptr);
     __syncthreads();
   }
 
@@ -502,16 +590,19 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
     int i = e % nr, t = e / nr;
     int gi = r0 + i;
     double x;
-    if constexpr (SCALED) {  // R back to F's scale (beta from FP64); V is scale-free
+    if constexpr (SCALED) {  // R back to F's scale (beta from FP64); V = x / v0 is scale-free
       const float f = Ps[t * cs + i];
-      x = gi == t ? s_beta[t] * s_up[t] : (gi < t ? scaled_float_to_double_any(f, s_ke[t]) : scaled_float_to_double(f, 0));
+      x = gi == t ? s_beta[t] * s_up[t]
+                  : (gi < t ? scaled_float_to_double_any(f, s_ke[t]) : scaled_float_to_double(f * s_iv[t], 0));
     } else {
       x = Ps[t * cs + i];
     }
     F[gi + t * ldf] = x;
     if constexpr (!TAIL) Vb[gi + t * ldv] = (gi < t) ? 0.0 : (gi == t ? 1.0 : x);
   }
-  if constexpr (TAIL) panel_tail(bw, cs, Ps, c, P, r0, nr, tau, counter, ctrl, tail, (unsigned)bw + base);
+  // grid barriers so far: FP32 panel the scale pass only, FP64 panel one per column
+  if constexpr (TAIL)
+    panel_tail(bw, cs, Ps, SCALED ? s_iv : nullptr, c, P, r0, nr, tau, counter, ctrl, tail, SCALED ? base : (unsigned)bw);
 }
 
 // ------------------------------------------------------------ T factor ----
@@ -712,7 +803,7 @@ int qr_plan(Arena &ar, int m, int n, int mode, QrWork *w) {
   w->Wp = ar.take<double>((size_t)QR_MAX_SPLITS * QR_B * (n > 0 ? n : 1));
   w->W2 = ar.take<double>((size_t)QR_B * (n > 0 ? n : 1));
   w->Gp = ar.take<double>((size_t)QR_MAX_SPLITS * QR_B * QR_B);
-  w->part = ar.take<double>((size_t)2 * di->num_sms * QR_B);
+  w->part = ar.take<double>((size_t)3 * di->num_sms * QR_B);
   w->rowk = ar.take<double>(2 * QR_B);
   w->counters = ar.take<unsigned>(npan > 0 ? npan : 1);
   return PURL_OK;
@@ -758,18 +849,12 @@ static int panel_tail_launch(int rows, int bw, double *Fp, int ldf, double *taup
                              const PanelTail &tail, const DeviceInfo *di, cudaStream_t s) {
   int P = panel_blocks(rows, di);
   int ch = ceil_div(rows, P);
-  // the panel's rows, their rounded copy V^, then one int per row (the
-  // transposed slices' exponents); without room for the copy, V^ is rounded in
-  // place at the end and its Gram columns formed there
-  PanelTail tl = tail;
+  // the panel's rows (V^ replaces them in the tail), then one int per row (the
+  // transposed slices' exponents)
   const size_t es_bytes = align_up((size_t)ch * sizeof(int), 16);
   const size_t cs = (size_t)(ch | 1);  // the kernel's column stride
-  size_t smem = 2 * cs * QR_B * sizeof(Real) + es_bytes;
-  tl.overlap = 1;
-  if (panel_capacity<true, Real>(di, smem) < P) {
-    smem = cs * QR_B * sizeof(Real) + es_bytes;
-    tl.overlap = 0;
-  }
+  const size_t smem = cs * QR_B * sizeof(Real) + es_bytes;
+  PanelTail tl = tail;
   int cap = panel_capacity<true, Real>(di, smem);
   if (cap < P) return PURL_ERR_UNSUPPORTED;
   int ldv = rows;

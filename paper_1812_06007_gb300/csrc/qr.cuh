@@ -28,7 +28,7 @@ struct QrWork {
 // column) and the T factor.
 struct PanelTail {
   int vexp = 1, P = 31;
-  int overlap = 1;  // set by panel_factor_tail: V^ kept in a second shared copy (else rounded in place)
+  unsigned epoch0 = 1;  // FP32 panel: epoch of column 0's tagged partial sums (see panel_kernel)
   Slices vs, vts;
   double *gpart = nullptr, *G = nullptr, *T = nullptr;
 };

@@ -500,6 +500,8 @@ int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t
   const InnerBufs b = {w.Vs, w.Vts, w.W2s, w.Pd};
   const int npan = ceil_div(n, QR_B);
   PURL_TRY(zero_async(w.base.counters, sizeof(unsigned) * npan, s));
+  // the FP32 panels' tagged partial sums: epoch 0 everywhere, panel p uses 1 + 32 p ...
+  PURL_TRY(zero_async(w.base.part, sizeof(double) * 2 * di->num_sms * QR_B, s));
   for (int J0 = 0, ob = 0; J0 < n; J0 += QR_NB, ++ob) {
     const int nbw = min(QR_NB, n - J0), rows = m - J0, nc_out = n - J0 - nbw;
     // inner panels, their updates confined to the outer block's columns
@@ -519,6 +521,7 @@ int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t
       tl.gpart = w.Gparts;
       tl.G = w.base.Gp;
       tl.T = Tp;
+      tl.epoch0 = 1u + 32u * (unsigned)p;
       PURL_TRY(panel_factor_tail(rj, bw, Fp, ldf, taup, w.base.counters + p, w.base, tl, s));
       PURL_TRY(apply_block_mixed(rj, bw, nc_in, Fp + (size_t)bw * ldf, ldf, w.Fs, j0, j0 + bw, w.col_exp, Tp, true,
                                  w, b, s));
