@@ -40,7 +40,7 @@ void choose_splits(int m, int n, int k, int num_sms, int *splits, int *k_chunk);
 
 namespace {
 
-constexpr int PNT = 256;  // panel kernel threads
+constexpr int PNT = 512;  // panel kernel threads
 constexpr int PW = PNT / 32;
 constexpr int kPanelMaxBlocks = 160;  // panel grids have at most this many blocks (>= the SM count)
 
@@ -382,6 +382,7 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
   }
   __syncthreads();
 
+  bool fused = false;  // FP32 panel: s_red already holds column k's partial sums
   for (int k = 0; k < bw; ++k) {
     const int buf = k & 1;
     Real *pb = parts + (size_t)buf * P * QR_B;
@@ -393,7 +394,8 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
     // column stride keeps the lanes' reads of one row on distinct banks); warp 0
     // adds the 8 row groups in a fixed order and publishes the block's
     // partials and, in the block holding it, row k.
-    {
+    // (The FP32 panel forms them inside the previous column's update.)
+    if (!SCALED || !fused) {
       Real s0 = 0, s1 = 0;
       if (lane >= k && lane < bw) {
         int i = i_lo + warp;
@@ -404,8 +406,8 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
         if (i < nr) s0 += Ps[k * cs + i] * Ps[lane * cs + i];
       }
       s_red[warp][lane] = s0 + s1;
+      __syncthreads();
     }
-    __syncthreads();
     const unsigned ep = tail.epoch0 + (unsigned)k;
     if (warp == 0) {
       Real S = 0;
@@ -523,16 +525,29 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
         }
       }
       __syncthreads();
+      fused = false;
       if (s_parf[0] != 0.0f) {
         // (d) a_t -= w_t v for t > k, v = x / v0 below row k and 1 at row k:
-        // thread (t = lane, g = warp) takes rows i_from + g, i_from + g + 8, ...
-        // Column k itself stays unscaled (v is formed where it is used).
+        // thread (t = lane, g = warp) takes rows i_from + g, i_from + g + PW, ...
+        // Column k itself stays unscaled (v is formed where it is used).  The
+        // warp shares each updated row, so lane t also accumulates the next
+        // column's partial sum x_{k+1,i} a_{t,i} over the rows below k + 1.
         const Real iv = s_parf[1];
         const Real w = (lane > k && lane < bw) ? s_w[lane] : Real(0);
+        const int kn = (k + 1) & 31;
+        Real s0 = 0;
         for (int i = max(0, k - r0) + warp; i < nr; i += PW) {
           const Real v = (r0 + i == k) ? Real(1) : Ps[k * cs + i] * iv;
-          if (lane > k && lane < bw) Ps[lane * cs + i] -= w * v;
+          Real a = Ps[lane * cs + i];
+          if (lane > k && lane < bw) {
+            a -= w * v;
+            Ps[lane * cs + i] = a;
+          }
+          const Real xn = __shfl_sync(0xffffffffu, a, kn);
+          if (r0 + i > k + 1) s0 += xn * a;
         }
+        s_red[warp][lane] = s0;
+        fused = true;
       }
       __syncthreads();
     } else {
