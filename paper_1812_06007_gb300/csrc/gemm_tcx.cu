@@ -46,10 +46,8 @@ int gemm_f64(bool ta, bool tb, int m, int n, int k, double alpha, const double *
 
 namespace {
 
-// warp 0 TMA, warp 1 MMA, warps 2-9 epilogue: two warps per 32-lane quadrant
-// of tensor memory, each draining half of the tile's columns
-constexpr int TCX_THREADS = 320;
-constexpr int TCX_EPI_WARPS = 8;
+// warp 0 TMA, warp 1 MMA, then the epilogue warps: EPI_WARPS / 4 per 32-lane
+// quadrant of tensor memory, each draining 16 of the tile's columns
 constexpr int TCX_KBC = 4;        // k-blocks per exact chunk (4 x 64 = 256 of K)
 constexpr int TCX_GROUP = 16;
 
@@ -69,6 +67,8 @@ struct TcxCfg {
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
   static constexpr int USED_COLS = 2 * CLASSES * BN;
   static constexpr int TMEM_COLS = USED_COLS <= 128 ? 128 : (USED_COLS <= 256 ? 256 : 512);
+  static constexpr int EPI_WARPS = BN / 4;  // 16 columns per epilogue warp
+  static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static_assert(STAGES >= 2, "stages");
   static_assert(USED_COLS <= 512, "tensor memory");
   static_assert(BN % 32 == 0, "BN");
@@ -91,7 +91,7 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
 }
 
 template <int S, bool ALL, int BN>
-__global__ void __launch_bounds__(TCX_THREADS, 1)
+__global__ void __launch_bounds__(TcxCfg<S, ALL, BN>::THREADS, 1)
     tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcView va,
                     TcView vb, int M, int N, int K, int k_chunk, int splits, const int *__restrict__ scA,
                     const int *__restrict__ scB, TcEpilogue ep, DeviceControl *ctrl) {
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull_bar[b], 1);
-      mbar_init(&tempty_bar[b], TCX_EPI_WARPS);
+      mbar_init(&tempty_bar[b], Cfg::EPI_WARPS);
     }
     mbar_init(&done_bar, 1);
     s_abort = 0;
@@ -290,9 +290,9 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
     }
   } else {
     // ---------------- epilogue: drain chunks into double-FP32 sums, then write ----------------
-    constexpr int HC = TCX_BN / 2;  // columns per epilogue warp
+    constexpr int HC = TCX_BN / (Cfg::EPI_WARPS / 4);  // columns per epilogue warp
     const int lane_base = 32 * (warp & 3);
-    const int cbase = ((warp - 2) >> 2) * HC;  // which half of the columns
+    const int cbase = ((warp - 2) >> 2) * HC;  // which part of the columns
     long long ct = 0;
     bool ok = true;
     for (long long work = blockIdx.x; work < total && ok; work += gridDim.x) {
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
       for (int j = 0; j < NW; ++j) accH[j] = accL[j] = 0;
       // the first batch of C is loaded before the wait for the tile's last
       // chunk, so its latency runs under that chunk's products
-      constexpr int BATCH = Cfg::WIDE ? 8 : 16;  // independent loads of C kept in flight
+      constexpr int BATCH = Cfg::WIDE || Cfg::EPI_WARPS > 8 ? 8 : 16;  // independent loads of C kept in flight
       constexpr int PRE = 8;                      // of which loaded early
       double cpre[PRE];
 #pragma unroll
@@ -547,7 +547,7 @@ int launch_tcx(const CUtensorMap &ma, const CUtensorMap &mb, TcView va, TcView v
                  (ep.mode == 0 ? 8.0 * M * N * (ep.beta != 0.0 ? 2 : 1) + (ep.out.base ? 2.0 * ep.out.S * M * N : 0)
                                : 8.0 * M * N * splits);
   LaunchScope ls(KC_GEMM_TC, s, flops, bytes, ep.tag ? ep.tag : "tcx_gemm_kernel");
-  tcx_gemm_kernel<S, ALL, BN><<<(unsigned)grid, TCX_THREADS, Cfg::SMEM, s>>>(ma, mb, va, vb, M, N, K, k_chunk,
+  tcx_gemm_kernel<S, ALL, BN><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(ma, mb, va, vb, M, N, K, k_chunk,
                                                                              splits, scA, scB, ep, ctrl);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
