@@ -46,8 +46,8 @@ int gemm_f64(bool ta, bool tb, int m, int n, int k, double alpha, const double *
 
 namespace {
 
-// warp 0 TMA, warp 1 MMA, then the epilogue warps: EPI_WARPS / 4 per 32-lane
-// quadrant of tensor memory, each draining 16 of the tile's columns
+// warp 0 TMA, warp 1 MMA, then 16 epilogue warps: 4 per 32-lane quadrant of
+// tensor memory, each draining a quarter of the tile's columns
 constexpr int TCX_KBC = 4;        // k-blocks per exact chunk (4 x 64 = 256 of K)
 constexpr int TCX_GROUP = 16;
 
@@ -67,7 +67,7 @@ struct TcxCfg {
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
   static constexpr int USED_COLS = 2 * CLASSES * BN;
   static constexpr int TMEM_COLS = USED_COLS <= 128 ? 128 : (USED_COLS <= 256 ? 256 : 512);
-  static constexpr int EPI_WARPS = BN / 4;  // 16 columns per epilogue warp
+  static constexpr int EPI_WARPS = 16;  // 4 per TMEM lane quadrant: BN / 4 columns each
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static_assert(STAGES >= 2, "stages");
   static_assert(USED_COLS <= 512, "tensor memory");
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(TcxCfg<S, ALL, BN>::THREADS, 1)
       for (int j = 0; j < NW; ++j) accH[j] = accL[j] = 0;
       // the first batch of C is loaded before the wait for the tile's last
       // chunk, so its latency runs under that chunk's products
-      constexpr int BATCH = Cfg::WIDE || Cfg::EPI_WARPS > 8 ? 8 : 16;  // independent loads of C kept in flight
+      constexpr int BATCH = HC < 8 ? HC : 8;  // independent loads of C kept in flight
       constexpr int PRE = 8;                      // of which loaded early
       double cpre[PRE];
 #pragma unroll
@@ -344,16 +344,16 @@ __global__ void __launch_bounds__(TcxCfg<S, ALL, BN>::THREADS, 1)
           const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)((b * Cfg::CLASSES + d) * TCX_BN + cbase);
           if constexpr (Cfg::WIDE) {
             // class sums are exact integers below 2^24 in magnitude
-            uint32_t v[16];
-            tmem_ld16(taddr, v);
+            uint32_t v[HC];
+            tmem_ld_cols<HC>(taddr, v);
             if (d < S - 4) {
               const int sh = 8 * (S - 5 - d);
 #pragma unroll
-              for (int j = 0; j < 16; ++j) accH[j] += (long long)__float2int_rz(__uint_as_float(v[j])) * (1LL << sh);
+              for (int j = 0; j < HC; ++j) accH[j] += (long long)__float2int_rz(__uint_as_float(v[j])) * (1LL << sh);
             } else {
               const int sh = 8 * (S - 1 - d);
 #pragma unroll
-              for (int j = 0; j < 16; ++j) accL[j] += (long long)__float2int_rz(__uint_as_float(v[j])) * (1LL << sh);
+              for (int j = 0; j < HC; ++j) accL[j] += (long long)__float2int_rz(__uint_as_float(v[j])) * (1LL << sh);
             }
             (void)w;
           } else if constexpr (HC >= 32) {
@@ -365,11 +365,10 @@ __global__ void __launch_bounds__(TcxCfg<S, ALL, BN>::THREADS, 1)
               for (int j = 0; j < 32; ++j) two_sum_acc(hi[h * 32 + j], lo[h * 32 + j], __uint_as_float(v[j]) * w);
             }
           } else {
-            static_assert(HC == 16, "half tile of 16 or a multiple of 32 columns");
-            uint32_t v[16];
-            tmem_ld16(taddr, v);
+            uint32_t v[HC];
+            tmem_ld_cols<HC>(taddr, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) two_sum_acc(hi[j], lo[j], __uint_as_float(v[j]) * w);
+            for (int j = 0; j < HC; ++j) two_sum_acc(hi[j], lo[j], __uint_as_float(v[j]) * w);
           }
         }
         tc_fence_before();
