@@ -172,16 +172,15 @@ __device__ __forceinline__ long long gram_entry(const int *a, const int *b, int 
   return s0 + s1;
 }
 
-// Slices, Gram matrix and T of a finished panel (see panel_kernel).  Ps holds
+// Slices and the Gram matrix of a finished panel (see panel_kernel).  Ps holds
 // the block's rows of the factored panel (F has been written): below the
 // diagonal V itself, or for the FP32 panel x with V = x viv[column]; V^
 // replaces them.  `nbar` grid barriers came before.
 template <typename Real>
-__device__ void panel_tail(int bw, int cs, Real *Ps, const float *viv, int c, int P, int r0, int nr, const double *tau,
+__device__ void panel_tail(int bw, int cs, Real *Ps, const float *viv, int c, int P, int r0, int nr,
                            unsigned *counter, DeviceControl *ctrl, const PanelTail &tl, unsigned nbar) {
   using V = TailV<Real>;
   constexpr bool EXACT = sizeof(Real) == 4;  // integer V^ and Gram matrix
-  __shared__ LarftSmem L;
   __shared__ unsigned char pa[QR_B * (QR_B + 1) / 2], pb[QR_B * (QR_B + 1) / 2];
   V *Vh = reinterpret_cast<V *>(Ps);
   int *es = reinterpret_cast<int *>(Vh + (size_t)cs * QR_B);  // the slab's row exponents after V^
@@ -237,40 +236,34 @@ __device__ void panel_tail(int bw, int cs, Real *Ps, const float *viv, int c, in
     else write_fixed_slices(Vh[t * cs + i], es[i], dst, tl.vts.plane, tl.vts.S);
   }
   if (!grid_barrier(counter, (nbar + 1) * P, ctrl)) return;
-  // (5) distributed sum over the blocks in a fixed order: warp w of block c
-  // takes entry c + P w (integer sums are exact, then scaled to V^'s unit
-  // squared and rounded once)
-  {
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int idx = c + P * warp; idx < npairs; idx += P * PW) {
-      if constexpr (EXACT) {
-        const long long *gp = reinterpret_cast<const long long *>(tl.gpart);
-        long long sum = 0;
-        for (int z = lane; z < P; z += 32) sum += __ldcg(&gp[(size_t)z * npairs + idx]);
+  // distributed sum over the blocks in a fixed order: warp w of block c takes
+  // entry c + P w, its lanes blocks lane, lane + 32, ... with independent loads
+  // (integer sums are exact, then scaled to V^'s unit squared and rounded once)
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int idx = c + P * warp; idx < npairs; idx += P * PW) {
+    constexpr int NZ = (kPanelMaxBlocks + 31) / 32;
+    if constexpr (EXACT) {
+      const long long *gp = reinterpret_cast<const long long *>(tl.gpart);
+      long long v[NZ], sum = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) __stcg(&tl.G[idx], int64_scaled_to_double(sum, 2 * (tl.vexp - tl.P)));
-      } else {
-        double sum = 0.0;
-        for (int z = lane; z < P; z += 32) sum += __ldcg(&tl.gpart[(size_t)z * npairs + idx]);
+      for (int u = 0; u < NZ; ++u) v[u] = lane + 32 * u < P ? __ldcg(&gp[(size_t)(lane + 32 * u) * npairs + idx]) : 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) __stcg(&tl.G[idx], sum);
-      }
+      for (int u = 0; u < NZ; ++u) sum += v[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) __stcg(&tl.G[idx], int64_scaled_to_double(sum, 2 * (tl.vexp - tl.P)));
+    } else {
+      double v[NZ], sum = 0.0;
+#pragma unroll
+      for (int u = 0; u < NZ; ++u)
+        v[u] = lane + 32 * u < P ? __ldcg(&tl.gpart[(size_t)(lane + 32 * u) * npairs + idx]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < NZ; ++u) sum += v[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) __stcg(&tl.G[idx], sum);
     }
   }
-  if (!grid_barrier(counter, (nbar + 2) * P, ctrl)) return;
-  if (c != 0) return;
-  // (6) block 0: T from the Gram matrix (tau_k = 2 / ||v^_k||^2)
-  for (int e = tid; e < QR_B * QR_B; e += PNT) L.Gm[e % QR_B][e / QR_B] = 0.0;
-  __syncthreads();
-  for (int idx = tid; idx < npairs; idx += PNT) {
-    const double g = __ldcg(&tl.G[idx]);
-    L.Gm[pa[idx]][pb[idx]] = g;
-    L.Gm[pb[idx]][pa[idx]] = g;
-  }
-  __syncthreads();
-  larft_core(bw, L, tau, tl.T, true);
 }
 
 // FP32 panel: beta = -sign(x0) ||x|| (R(j,j)) and tau = |v0| / ||x|| of column j
@@ -616,8 +609,9 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
     if constexpr (!TAIL) Vb[gi + t * ldv] = (gi < t) ? 0.0 : (gi == t ? 1.0 : x);
   }
   // grid barriers so far: FP32 panel the scale pass only, FP64 panel one per column
+  // grid barriers so far: FP32 panel the scale pass only, FP64 panel one per column
   if constexpr (TAIL)
-    panel_tail(bw, cs, Ps, SCALED ? s_iv : nullptr, c, P, r0, nr, tau, counter, ctrl, tail, SCALED ? base : (unsigned)bw);
+    panel_tail(bw, cs, Ps, SCALED ? s_iv : nullptr, c, P, r0, nr, counter, ctrl, tail, SCALED ? base : (unsigned)bw);
 }
 
 // ------------------------------------------------------------ T factor ----
@@ -654,6 +648,28 @@ __global__ void __launch_bounds__(256) larft_kernel(int bw, int splits, const do
   }
   __syncthreads();
   larft_core(bw, L, tau, T, tau_from_gram);
+}
+
+// T factor of a tensor-core QR panel from the Gram matrix of its rounded
+// vectors (upper triangle column by column, as the panel's tail sums it):
+// tau_k = 2 / ||v^_k||^2.  One block; it runs beside the next kernels of the QR,
+// which do not need T.
+__global__ void __launch_bounds__(PNT) panel_t_kernel(int bw, const double *__restrict__ G,
+                                                      const double *__restrict__ tau, double *T) {
+  __shared__ LarftSmem L;
+  const int tid = threadIdx.x;
+  const int npairs = bw * (bw + 1) / 2;
+  for (int e = tid; e < QR_B * QR_B; e += PNT) L.Gm[e % QR_B][e / QR_B] = 0.0;
+  __syncthreads();
+  for (int idx = tid; idx < npairs; idx += PNT) {
+    int b = 0, a = idx;  // (a, b), a <= b, column by column
+    while (a > b) { a -= b + 1; ++b; }
+    const double g = __ldcg(&G[idx]);
+    L.Gm[a][b] = g;
+    L.Gm[b][a] = g;
+  }
+  __syncthreads();
+  larft_core(bw, L, tau, T, true);
 }
 
 // W2(:, c) = op(T) * sum_z Wp_z(:, c); op(T) = T^T when trans, else T.
@@ -881,6 +897,14 @@ static int panel_tail_launch(int rows, int bw, double *Fp, int ldf, double *taup
                  "panel_kernel");
   PURL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)panel_kernel<true, Real>, dim3(P), dim3(PNT), args, smem, s));
   return PURL_OK;
+}
+
+// T of the panel whose tail wrote tail.G, on stream s.
+int panel_t(int rows, int bw, const double *taup, const PanelTail &tail, cudaStream_t s) {
+  (void)rows;
+  LaunchScope ls(KC_OTHER, s, 0.0, 8.0 * bw * (bw + 1) / 2.0, "panel_t_kernel");
+  panel_t_kernel<<<1, PNT, 0, s>>>(bw, tail.G, taup, tail.T);
+  return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 
 // The panel runs in FP32 (FP64 reflector parameters) when V^ carries at most

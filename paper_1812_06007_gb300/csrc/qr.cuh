@@ -24,8 +24,8 @@ struct QrWork {
 // Outputs of the tensor-core QR's fused panel tail (see panel_kernel): the
 // Householder vectors rounded to the grid 2^(vexp - P), their slices vs
 // (natural) and vts (transposed, one exponent per row), the Gram matrix
-// partials gpart (blocks x bw(bw+1)/2), its sum G (upper triangle, column by
-// column) and the T factor.
+// partials gpart (blocks x bw(bw+1)/2) and their sum G (upper triangle column
+// by column); panel_t then writes the T factor from G.
 struct PanelTail {
   int vexp = 1, P = 31;
   unsigned epoch0 = 1;  // FP32 panel: epoch of column 0's tagged partial sums (see panel_kernel)
@@ -38,6 +38,8 @@ int qr_plan(Arena &ar, int m, int n, int mode, QrWork *w);
 // outputs written; w.Vb is not).
 int panel_factor_tail(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *counter, QrWork &w,
                       const PanelTail &tail, cudaStream_t s);
+// The panel's T from the Gram matrix its tail wrote (one block; tail.T).
+int panel_t(int rows, int bw, const double *taup, const PanelTail &tail, cudaStream_t s);
 int panel_factor(int rows, int bw, double *Fp, int ldf, double *taup, unsigned *counter, QrWork &w,
                  cudaStream_t s);
 int larft_from_gram(int bw, int splits, const double *Gp, const double *taup, double *Tp, cudaStream_t s,

@@ -28,6 +28,8 @@
 //     instead of n / QR_B times.  T_out is assembled from the panels' T_k and
 //     the exact Gram matrix of the rounded V (every slice pair).  Q is formed
 //     from the outer blocks only.
+#include <map>
+
 #include "profile.cuh"
 #include "qr_mixed.cuh"
 #include "slice_int.cuh"
@@ -319,7 +321,8 @@ struct InnerBufs {
 // column (its current maximum, written to cexp[c0 + c]): an entry's slicing
 // error is then 2^-8S of its column's largest entry, not of the column norm.
 int apply_block_mixed(int rows, int bw, int nc, double *Cp, int ldc, const Slices &Cs, int r0, int c0,
-                      int *cexp, const double *T, bool trans, QrMixWork &w, const InnerBufs &b, cudaStream_t s) {
+                      int *cexp, const double *T, bool trans, QrMixWork &w, const InnerBufs &b, cudaStream_t s,
+                      cudaEvent_t t_ready) {
   if (nc <= 0 || rows <= 0 || bw <= 0) return PURL_OK;
   const DeviceInfo *di = device_info();
   Slices view = Cs;
@@ -334,7 +337,8 @@ int apply_block_mixed(int rows, int bw, int nc, double *Cp, int ldc, const Slice
   ep.Pd = b.Pd;
   ep.tag = "tcx inner V^T C";
   PURL_TRY(tcx_gemm_view(Cs, r0, c0, b.Vs, 0, 0, nc, bw, rows, w.S, ep, sp, ch, s));
-  // W2 = op(T) W, sliced
+  // W2 = op(T) W, sliced (T formed on another stream until t_ready)
+  if (t_ready) PURL_CUDA_TRY(cudaStreamWaitEvent(s, t_ready, 0));
   { LaunchScope ls(KC_OTHER, s, 2.0 * bw * bw * (double)nc, 8.0 * sp * (double)nc * bw, "reduce_tmul_slices_kernel");
     reduce_tmul_slices_kernel<<<ceil_div(nc, kTmulCols), 256, 0, s>>>(bw, nc, sp, b.Pd, T, trans, b.W2s); }
   PURL_CUDA_TRY(cudaGetLastError());
@@ -493,12 +497,40 @@ int qr_mixed_plan(Arena &ar, int m, int n, int S, QrMixWork *w) {
   return PURL_OK;
 }
 
+namespace {
+
+// A second stream of the calling host thread on the current device, with two
+// events: the panels' T factors are formed on it beside the first kernels of
+// each inner update, which do not need them.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t panel_done = nullptr, t_done = nullptr;
+};
+
+int side_stream(SideStream **out) {
+  thread_local std::map<int, SideStream> per_device;
+  int dev = 0;
+  PURL_CUDA_TRY(cudaGetDevice(&dev));
+  SideStream &ss = per_device[dev];
+  if (!ss.s) {
+    PURL_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+    PURL_CUDA_TRY(cudaEventCreateWithFlags(&ss.panel_done, cudaEventDisableTiming));
+    PURL_CUDA_TRY(cudaEventCreateWithFlags(&ss.t_done, cudaEventDisableTiming));
+  }
+  *out = &ss;
+  return PURL_OK;
+}
+
+}  // namespace
+
 int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t s) {
   const DeviceInfo *di = device_info();
   if (!di) return PURL_ERR_CUDA;
   if (n == 0) return PURL_OK;
   const InnerBufs b = {w.Vs, w.Vts, w.W2s, w.Pd};
   const int npan = ceil_div(n, QR_B);
+  SideStream *side = nullptr;
+  PURL_TRY(side_stream(&side));
   PURL_TRY(zero_async(w.base.counters, sizeof(unsigned) * npan, s));
   // the FP32 panels' tagged partial sums: epoch 0 everywhere, panel p uses 1 + 32 p ...
   PURL_TRY(zero_async(w.base.part, sizeof(double) * 2 * di->num_sms * QR_B, s));
@@ -510,8 +542,9 @@ int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t
       const int nc_in = J0 + nbw - j0 - bw;
       double *Fp = F + j0 + (size_t)j0 * ldf;
       double *taup = w.base.tau + j0;
-      // the panel, with its rounded V^, V^'s slices, the FP64 Gram matrix of V^
-      // and T_k (tau_k = 2 / ||v^_k||^2) formed in the same cooperative launch
+      // the panel, with its rounded V^, V^'s slices and V^'s Gram matrix in the
+      // same cooperative launch; T_k (tau_k = 2 / ||v^_k||^2) from the Gram
+      // matrix on the side stream, waited for just before its first use
       double *Tp = w.base.T + (size_t)p * QR_B * QR_B;
       PanelTail tl;
       tl.vexp = kVExp;
@@ -523,8 +556,14 @@ int qr_mixed_factor(int m, int n, double *F, int ldf, QrMixWork &w, cudaStream_t
       tl.T = Tp;
       tl.epoch0 = 1u + 32u * (unsigned)p;
       PURL_TRY(panel_factor_tail(rj, bw, Fp, ldf, taup, w.base.counters + p, w.base, tl, s));
+      PURL_CUDA_TRY(cudaEventRecord(side->panel_done, s));
+      PURL_CUDA_TRY(cudaStreamWaitEvent(side->s, side->panel_done, 0));
+      PURL_TRY(panel_t(rj, bw, taup, tl, side->s));
+      PURL_CUDA_TRY(cudaEventRecord(side->t_done, side->s));
       PURL_TRY(apply_block_mixed(rj, bw, nc_in, Fp + (size_t)bw * ldf, ldf, w.Fs, j0, j0 + bw, w.col_exp, Tp, true,
-                                 w, b, s));
+                                 w, b, s, side->t_done));
+      // T_k is in place (and the Gram matrix free) before the next panel
+      PURL_CUDA_TRY(cudaStreamWaitEvent(s, side->t_done, 0));
     }
     // one aggregated update of everything to the right of the outer block
     double *Tout = w.Tout + (size_t)ob * QR_NB * QR_NB;

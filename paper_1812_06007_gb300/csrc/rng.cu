@@ -16,7 +16,10 @@ __device__ __forceinline__ double u53(uint64_t x) {
   return (static_cast<double>(x >> 11) + 0.5) * 0x1.0p-53;
 }
 
-// One thread per Philox block: 4 consecutive (column-major) elements.
+// One thread per Philox block: 4 consecutive (column-major) elements.  F32:
+// the same words through the FP32 Box-Muller of gaussian_block_f32 (stored as
+// FP64), for the paths whose first use of G rounds it to 16 bits.
+template <bool F32>
 __global__ void __launch_bounds__(256) gaussian_kernel(uint64_t seed, uint64_t stream_id,
                                                        int rows, long long count, double *G,
                                                        long long ldg) {
@@ -24,16 +27,23 @@ __global__ void __launch_bounds__(256) gaussian_kernel(uint64_t seed, uint64_t s
   long long nblk = (count + 3) / 4;
   for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nblk;
        b += (long long)gridDim.x * blockDim.x) {
-    uint64_t c[4] = {static_cast<uint64_t>(b), 0, 0, 0};
-    philox4x64_10(c, seed, stream_id);
     double z[4];
+    if constexpr (F32) {
+      float zf[4];
+      gaussian_block_f32(seed, stream_id, (uint64_t)b, zf);
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      double r = sqrt(-2.0 * log(u53(c[2 * p])));
-      double s, co;
-      sincos(two_pi * u53(c[2 * p + 1]), &s, &co);
-      z[2 * p] = r * co;
-      z[2 * p + 1] = r * s;
+      for (int t = 0; t < 4; ++t) z[t] = zf[t];
+    } else {
+      uint64_t c[4] = {static_cast<uint64_t>(b), 0, 0, 0};
+      philox4x64_10(c, seed, stream_id);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        double r = sqrt(-2.0 * log(u53(c[2 * p])));
+        double s, co;
+        sincos(two_pi * u53(c[2 * p + 1]), &s, &co);
+        z[2 * p] = r * co;
+        z[2 * p + 1] = r * s;
+      }
     }
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -46,7 +56,7 @@ __global__ void __launch_bounds__(256) gaussian_kernel(uint64_t seed, uint64_t s
 }  // namespace
 
 int launch_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double *G, int ldg,
-                    cudaStream_t stream) {
+                    cudaStream_t stream, bool fp32_math) {
   long long count = (long long)rows * cols;
   if (count == 0) return PURL_OK;
   const DeviceInfo *di = device_info();
@@ -55,7 +65,8 @@ int launch_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, doubl
   long long want = (nblk + 255) / 256;
   int grid = (int)(want < (long long)di->num_sms * 8 ? want : (long long)di->num_sms * 8);
   LaunchScope ls(KC_OTHER, stream, 0.0, 8.0 * count, "gaussian_kernel");
-  gaussian_kernel<<<grid, 256, 0, stream>>>(seed, stream_id, rows, count, G, ldg);
+  if (fp32_math) gaussian_kernel<true><<<grid, 256, 0, stream>>>(seed, stream_id, rows, count, G, ldg);
+  else gaussian_kernel<false><<<grid, 256, 0, stream>>>(seed, stream_id, rows, count, G, ldg);
   return cudaGetLastError() == cudaSuccess ? PURL_OK : PURL_ERR_CUDA;
 }
 

@@ -22,4 +22,24 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64
   }
 }
 
+// FP32 normal deviates of one Philox block: the 53-bit uniform
+// ((w >> 11) + 0.5) 2^-53 of the FP64 generator, rounded once to FP32, then
+// Box-Muller with FP32 logf / sincospif.
+__device__ __forceinline__ float u53_f32(uint64_t w) {
+  return __ull2float_rn(2ull * (w >> 11) + 1ull) * 0x1.0p-54f;
+}
+
+__device__ __forceinline__ void gaussian_block_f32(uint64_t seed, uint64_t stream_id, uint64_t b, float z[4]) {
+  uint64_t c[4] = {b, 0, 0, 0};
+  philox4x64_10(c, seed, stream_id);
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const float r = sqrtf(-2.f * logf(u53_f32(c[2 * p])));
+    float s, co;
+    sincospif(2.f * u53_f32(c[2 * p + 1]), &s, &co);
+    z[2 * p] = r * co;
+    z[2 * p + 1] = r * s;
+  }
+}
+
 }  // namespace purl

@@ -19,7 +19,8 @@
 
 namespace purl {
 
-int launch_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double *G, int ldg, cudaStream_t stream);
+int launch_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double *G, int ldg, cudaStream_t stream,
+                    bool fp32_math = false);
 int gemm_f64(bool ta, bool tb, int m, int n, int k, double alpha, const double *A, int lda, const double *B, int ldb,
              double beta, double *C, int ldc, cudaStream_t s);
 

@@ -18,7 +18,7 @@
 namespace purl {
 
 int launch_gaussian(uint64_t seed, uint64_t stream_id, int rows, int cols, double *G, int ldg,
-                    cudaStream_t stream);
+                    cudaStream_t stream, bool fp32_math = false);
 int gemm_f64(bool ta, bool tb, int m, int n, int k, double alpha, const double *A, int lda,
              const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s);
 
@@ -202,7 +202,9 @@ static int urv_run_mixed(int m, int n, const double *A, int lda, int q, int reor
     PURL_TRY(split_scaled(m, n, A, lda, w.At1, w.pexp, true, s));   // operand of A Y   (rows n = K, cols m = M)
     PURL_TRY(split_scaled(m, n, A, lda, w.An1, w.pexp, false, s));  // operand of A^T Z (rows m = K, cols n = M)
   }
-  PURL_TRY(launch_gaussian(seed, 0, n, n, Y, n, s));
+  // G through the FP32 Box-Muller: its first use rounds it to BF16 / FP16
+  // (with q = 0 it is orthonormalised by the mixed QR, whose panels are FP32)
+  PURL_TRY(launch_gaussian(seed, 0, n, n, Y, n, s, true));
   for (int i = 1; i <= q; ++i) {
     PURL_TRY(split_scaled(n, n, Y, n, w.Ys, w.pexp, false, s));
     ep.C = F;
