@@ -524,19 +524,35 @@ def _peaks():
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel function, averaged
 # over every launch of one ncu capture of the bench's own step (summary and command under profiles/).
-# It is reported only while the kernel's source file still has the hash it had when captured.
+# It is reported only while the source that determines the kernel's traffic -- its configuration, the
+# kernel, its launch and the tile dispatch, as regions of its source file -- still has the hash it had
+# when captured.
 TRAFFIC = {
-    # 5906 launches of one mixed n = 16384 factorization: 767.97 GB read + 234.00 GB written
-    "tcx_gemm_kernel": {"src": "paper_1812_06007_gb300/csrc/gemm_tcx.cu", "sha16": "e24fc7c040835423",
-                        "bytes_per_launch": 169.65e6,
-                        "profile": "profiles/ncu_tcx_gemm_kernel_traffic_mixed_n16384.md"},
+    # 5906 launches of one mixed n = 16384 factorization: 770.37 GB read + 235.18 GB written
+    "tcx_gemm_kernel": {
+        "src": "paper_1812_06007_gb300/csrc/gemm_tcx.cu",
+        "regions": [("template <int S, bool ALL, int BN>\nstruct TcxCfg {",
+                     "template <int S>\n__global__ void __launch_bounds__(256) split_exact_kernel("),
+                    ("template <int S, bool ALL, int BN>\nint launch_tcx(", "}  // namespace\n"),
+                    ("int tcx_gemm_view_impl(", "int tcx_gemm_view(")],
+        "sha16": "4a8910c1a36b76ea",
+        "bytes_per_launch": 170.26e6,
+        "profile": "profiles/ncu_tcx_gemm_kernel_traffic_mixed_n16384.md"},
 }
 
 
-def _sha16(path: str) -> str:
+def _region_sha16(path: str, regions) -> str:
+    """sha256 (16 hex digits) of the concatenated text regions [start, end) of a source file, each
+    from the first occurrence of its start marker (after the previous region) to its end marker."""
     import hashlib
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    with open(path, encoding="utf-8") as f:
+        text = f.read()
+    h = hashlib.sha256()
+    for start, end in regions:
+        a = text.index(start)
+        b = text.index(end, a + len(start))
+        h.update(text[a:b].encode("utf-8"))
+    return h.hexdigest()[:16]
 
 
 def attach_traffic(roof):
@@ -544,8 +560,8 @@ def attach_traffic(roof):
     if not t:
         return
     try:
-        same = _sha16(os.path.join(ROOT, t["src"])) == t["sha16"]
-    except OSError:
+        same = _region_sha16(os.path.join(ROOT, t["src"]), t["regions"]) == t["sha16"]
+    except (OSError, ValueError):
         same = False
     if same:
         roof["traffic"] = t["bytes_per_launch"]
