@@ -296,9 +296,10 @@ __device__ __forceinline__ void panel_beta_tau(int j, const float2 *sx, double *
 // TAIL (the tensor-core QR's panel): after the columns, the blocks also round
 // the Householder vectors to the grid 2^(vexp - P) (V^), write V^'s fixed-point
 // slices (natural, exponent vexp per column; transposed, the exponent of each
-// row's largest entry), form the FP64 Gram matrix V^T V^ (per-block partials,
-// one grid barrier, a distributed sum, another barrier) and block 0 builds T
-// from it with tau_k = 2 / ||v^_k||^2.  Without TAIL the explicit V goes to Vb.
+// row's largest entry) and form the Gram matrix V^T V^ (per-block partials,
+// exact 64-bit integer sums for the FP32 panel, FP64 otherwise; one grid
+// barrier and a distributed sum); T follows from it in panel_t_kernel with
+// tau_k = 2 / ||v^_k||^2.  Without TAIL the explicit V goes to Vb.
 template <bool TAIL, typename Real>
 __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, double *F,
                                                     long long ldf, double *Vb, long long ldv,
@@ -608,7 +609,6 @@ __global__ void __launch_bounds__(PNT) panel_kernel(int rows, int bw, int ch, do
     F[gi + t * ldf] = x;
     if constexpr (!TAIL) Vb[gi + t * ldv] = (gi < t) ? 0.0 : (gi == t ? 1.0 : x);
   }
-  // grid barriers so far: FP32 panel the scale pass only, FP64 panel one per column
   // grid barriers so far: FP32 panel the scale pass only, FP64 panel one per column
   if constexpr (TAIL)
     panel_tail(bw, cs, Ps, SCALED ? s_iv : nullptr, c, P, r0, nr, counter, ctrl, tail, SCALED ? base : (unsigned)bw);

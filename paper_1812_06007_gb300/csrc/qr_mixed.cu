@@ -1,10 +1,11 @@
 // qr_mixed.cu -- blocked Householder QR for the mixed-precision mode.
 //
-// Same algorithm as qr.cu (Section 2.2's blocked unpivoted QR): FP64
-// Householder panels, compact-WY blocks, trailing update C <- (I - V T^T V^T) C,
-// explicit Q by applying the blocks last to first.  What changes is the
-// arithmetic of the level-3 products, which run on the BF16 tensor cores with
-// exact accumulation (gemm_tcx.cu) over S fixed-point slices:
+// Same algorithm as qr.cu (Section 2.2's blocked unpivoted QR): Householder
+// panels (FP32 arithmetic with FP64 beta and tau at up to 4 slices, FP64 at 8),
+// compact-WY blocks, trailing update C <- (I - V T^T V^T) C, explicit Q by
+// applying the blocks last to first.  What changes is the arithmetic of the
+// level-3 products, which run on the BF16 tensor cores with exact
+// accumulation (gemm_tcx.cu) over S fixed-point slices:
 //
 //   * the matrix being factored (or the Q being formed) keeps FP64 values,
 //     read by the panels and rewritten by every trailing update; before each
@@ -13,13 +14,14 @@
 //     carried to 2^-8S of the largest entry of its column;
 //   * V is rounded to a fixed grid (V^) that every slicing of it represents
 //     exactly, so V^T C, the update and the Gram matrix all see the same V^;
-//     T is built from the FP64 Gram matrix of V^ with tau_k = 2/||v^_k||^2,
+//     T is built from the Gram matrix of V^ (exact in 64-bit integers at up
+//     to 4 slices) with tau_k = 2/||v^_k||^2,
 //     so every applied block is orthogonal for the vectors it actually uses
 //     (the slice pairs the tensor-core products drop would make a tensor-core
 //     Gram matrix miss this by ~2^-8S);
 //   * W = V^T C comes out as FP64 split-K partials, is multiplied by op(T) in
 //     FP64 and re-sliced (per-column scale) for the update C - V W2;
-//   * two levels of blocking: QR_B-column FP64 panels are grouped into
+//   * two levels of blocking: QR_B-column panels are grouped into
 //     QR_NB-column outer blocks.  Inside an outer block the panels update only
 //     the block's own columns (a slab that stays in L2); the rest of the
 //     matrix receives ONE update per outer block with the aggregated
